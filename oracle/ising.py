@@ -1,0 +1,144 @@
+"""2D Ising model: site tensor and exact partition functions (oracle).
+
+Test infrastructure only: nothing on the product path may import this module.
+
+Model (Sec. IV, Eq. ising_model, extended by a uniform field h):
+    Z = sum_{sigma} exp( beta * sum_<ij> s_i s_j + beta * h * sum_i s_i )
+on an L x L periodic square lattice, J = k_B = 1, beta = 1/T.
+
+Exact references used to pin the Monte Carlo estimator:
+  * brute_force_lnZ    - direct sum over all 2^(L*L) states (L <= 4)
+  * transfer_lnZ       - row transfer matrix, Z = Tr T^L (L <= 10)
+  * kaufman_lnZ        - Kaufman's closed form for the finite torus, h = 0
+  * onsager_minus_beta_f - Onsager's free energy per site, h = 0, L -> inf
+"""
+import itertools
+import math
+
+import numpy as np
+
+
+def site_tensor(beta, h):
+    """T[l,u,r,d] = sum_s e^{beta h s} W[s,l] W[s,u] W[s,r] W[s,d].
+
+    The bond weight e^{beta s s'} = sum_a W[s,a] W[s',a] with
+    W[s,0] = sqrt(cosh beta), W[s,1] = s sqrt(sinh beta); index s = 0 is spin
+    +1 and s = 1 is spin -1.  Each bond of the lattice is shared by the r leg
+    of one site and the l leg of its right neighbour (d and u vertically), so
+    the trace of the network of these tensors is Z.
+    """
+    W = np.array([[math.sqrt(math.cosh(beta)), math.sqrt(math.sinh(beta))],
+                  [math.sqrt(math.cosh(beta)), -math.sqrt(math.sinh(beta))]])
+    T = np.zeros((2, 2, 2, 2))
+    for s, spin in enumerate((1.0, -1.0)):
+        w = W[s]
+        T += math.exp(beta * h * spin) * np.einsum('a,b,c,d->abcd', w, w, w, w)
+    return T
+
+
+def _logsumexp(x):
+    m = np.max(x)
+    return float(m + np.log(np.sum(np.exp(x - m))))
+
+
+def brute_force_lnZ(L, beta, h=0.0):
+    """ln Z by enumerating every spin configuration (2^(L^2) states)."""
+    n = L * L
+    if n > 20:
+        raise ValueError("brute force limited to L*L <= 20")
+    idx = np.arange(1 << n, dtype=np.int64)
+    spins = 1 - 2 * ((idx[:, None] >> np.arange(n)) & 1)          # (states, n)
+    spins = spins.reshape(-1, L, L)                                 # [state, y, x]
+    bonds = (spins * np.roll(spins, -1, axis=2)).sum(axis=(1, 2)) \
+        + (spins * np.roll(spins, -1, axis=1)).sum(axis=(1, 2))
+    mag = spins.sum(axis=(1, 2))
+    return _logsumexp(beta * bonds + beta * h * mag)
+
+
+def transfer_lnZ(L, beta, h=0.0):
+    """ln Z = ln Tr(T^L) with the 2^L x 2^L row-to-row transfer matrix."""
+    if L > 10:
+        raise ValueError("transfer matrix limited to L <= 10")
+    rows = list(itertools.product((1, -1), repeat=L))
+    R = np.array(rows, dtype=np.float64)                            # (2^L, L)
+    intra = (R * np.roll(R, -1, axis=1)).sum(axis=1)                # horizontal bonds
+    field = R.sum(axis=1)
+    inter = R @ R.T                                                 # vertical bonds
+    logT = beta * inter + beta * (intra + h * field)[:, None]
+    # T[R,R'] carries row R's horizontal bonds and field plus the R-R' vertical bonds
+    shift = logT.max()
+    T = np.exp(logT - shift)
+    ev = np.linalg.eigvals(T)
+    s = np.sum(ev.astype(np.complex128) ** L)
+    return float(L * shift + np.log(s.real))
+
+
+def kaufman_lnZ(L, beta, M=None):
+    """ln Z of the h = 0 Ising model on an M x L torus (M rows, default M = L).
+
+    Kaufman, Phys. Rev. 76, 1232 (1949):
+      Z = 1/2 (2 sinh 2K)^{ML/2} (Z1 + Z2 + Z3 + Z4),
+      Z1 = prod_{r<L} 2 cosh(M g_{2r+1}/2),  Z2 = prod 2 sinh(M g_{2r+1}/2),
+      Z3 = prod_{r<L} 2 cosh(M g_{2r}/2),    Z4 = prod 2 sinh(M g_{2r}/2),
+      cosh g_k = cosh 2K coth 2K - cos(pi k / L)  (g_k > 0, k != 0),
+      g_0 = 2K + ln tanh K  (signed).
+    Evaluated with signed logarithms so that large L does not overflow.
+    """
+    if M is None:
+        M = L
+    K = float(beta)
+    c = math.cosh(2 * K) / math.tanh(2 * K)
+
+    def gamma(k):
+        if k % (2 * L) == 0:
+            return 2 * K + math.log(math.tanh(K))
+        return math.acosh(c - math.cos(math.pi * k / L))
+
+    terms = []                      # (sign, log|Z_i|)
+    for odd in (1, 0):
+        g = [gamma(2 * r + odd) for r in range(L)]
+        lc = sum(math.log(2 * math.cosh(M * x / 2)) for x in g)
+        terms.append((1.0, lc))
+        sg, ls = 1.0, 0.0
+        for x in g:
+            v = 2 * math.sinh(M * x / 2)
+            if v == 0.0:
+                sg = 0.0
+                break
+            sg *= math.copysign(1.0, v)
+            ls += math.log(abs(v))
+        terms.append((sg, ls))
+    m = max(t[1] for t in terms)
+    tot = sum(sg * math.exp(lv - m) for sg, lv in terms)
+    return math.log(0.5) + (M * L / 2) * math.log(2 * math.sinh(2 * K)) + m + math.log(tot)
+
+
+def onsager_minus_beta_f(beta, npts=4096):
+    """-beta f per site in the thermodynamic limit, h = 0 (Onsager 1944).
+
+    -beta f = ln 2 + 1/(8 pi^2) Int_0^{2pi} Int_0^{2pi}
+              ln[cosh^2 2K - sinh 2K (cos t1 + cos t2)] dt1 dt2,
+    evaluated with the midpoint rule on a periodic grid (spectrally accurate
+    away from the critical point).
+    """
+    K = float(beta)
+    t = (np.arange(npts) + 0.5) * (2 * np.pi / npts)
+    c = np.cos(t)
+    a = math.cosh(2 * K) ** 2
+    b = math.sinh(2 * K)
+    acc = 0.0
+    for c1 in c:
+        acc += np.log(a - b * (c1 + c)).sum()
+    return math.log(2.0) + acc / (npts * npts) / 2.0
+
+
+def onsager_minus_beta_f_1d(beta):
+    """Same quantity from the one-dimensional elliptic form:
+    -beta f = ln(2 cosh 2K) + (1/pi) Int_0^{pi/2} ln[(1 + sqrt(1 - k^2 sin^2 t))/2] dt,
+    k = 2 sinh 2K / cosh^2 2K.  Used only to cross-check the 2D integral."""
+    from scipy.integrate import quad
+    K = float(beta)
+    k = 2 * math.sinh(2 * K) / math.cosh(2 * K) ** 2
+    f = lambda t: math.log((1 + math.sqrt(max(0.0, 1 - (k * math.sin(t)) ** 2))) / 2)
+    val, _ = quad(f, 0, math.pi / 2, limit=200, epsabs=1e-14, epsrel=1e-14)
+    return math.log(2 * math.cosh(2 * K)) + val / math.pi

@@ -1,0 +1,177 @@
+"""Monte Carlo TRG trajectories (oracle), Secs. II-III.
+
+Test infrastructure only: nothing on the product path may import this module.
+
+One trajectory coarse-grains the whole L x L network level by level
+(Levin-Nave TRG, Sec. III), replacing every truncated SVD by the stochastic
+truncation of Sec. II, sampled independently for every tensor (Sec. III: the
+samples of different tensors must be independent).  After 2 log2(L) levels a
+single tensor remains and is traced (Sec. IV).  Its value Z~ is an unbiased
+sample of Z (Sec. III, Eq. infiniteEnsemble).
+
+Readings of points the paper leaves open (shared with the device path by
+specification):
+  * the SVD is LAPACK's (numpy.linalg.svd), singular values descending;
+  * every tensor is divided by its largest singular value s_1 after its SVD
+    and ln s_1 is accumulated per trajectory (range control only);
+  * the reweighted value s_i / r_i is split as its square root on each side;
+  * bond dimension of level k+1:  D' = min(chi, nu), where nu is the larger
+    nonzero count of the two sublattice matricizations when every level-k
+    tensor is identical (the shared prefix), else D_k^2; halves with fewer
+    kept values are zero-padded to D';
+  * the result is (sign, ln|Z~|, flags); flags mark near-ties where two
+    correct implementations may legitimately keep different indices.
+"""
+import math
+
+import numpy as np
+
+from . import philox
+from .network import plan
+from .sampler import truncate
+
+
+def matricize(T, parity):
+    """A (parity 0): M[(l,u),(r,d)];  B (parity 1): M[(u,r),(d,l)]."""
+    D = T.shape[0]
+    if parity == 0:
+        return T.reshape(D * D, D * D)
+    return T.transpose(1, 2, 3, 0).reshape(D * D, D * D)
+
+
+def svd(M):
+    U, s, Vt = np.linalg.svd(M, full_matrices=False)
+    return U, s, Vt
+
+
+def split(T, parity, Dn, choose):
+    """Split one tensor into its two three-leg halves (Sec. II + Sec. III).
+
+    choose(s, n_rows) -> (kept, reweighted values, flags).  Returns
+    (left half [x,y,Dn], right half [Dn,x,y], ln s_1, flags) where the left
+    half is F1[l,u,a] (A) or F2[u,r,b] (B) and the right half F3[a,r,d] (A)
+    or F4[b,d,l] (B).  A zero tensor gives ln s_1 = -inf.
+    """
+    D = T.shape[0]
+    M = matricize(T, parity)
+    U, s, Vt = svd(M)
+    s1 = s[0]
+    if not s1 > 0.0:
+        z = np.zeros((D, D, Dn))
+        return z, np.zeros((Dn, D, D)), -math.inf, 0
+    kept, st, flags = choose(s / s1, D * D)
+    if len(kept) > Dn:
+        raise AssertionError("kept more values than the bond dimension")
+    root = np.sqrt(st)
+    left = np.zeros((D * D, Dn))
+    right = np.zeros((Dn, D * D))
+    left[:, :len(kept)] = U[:, kept] * root
+    right[:len(kept), :] = root[:, None] * Vt[kept, :]
+    return left.reshape(D, D, Dn), right.reshape(Dn, D, D), math.log(s1), flags
+
+
+def contract(F3, F4, F2, F1):
+    """T'[al,be,de,ga] = sum F3[al,i,j] F4[be,k,i] F2[j,m,ga] F1[m,k,de]."""
+    return np.einsum('aij,bki,jmg,mkd->abdg', F3, F4, F2, F1)
+
+
+class Problem:
+    """A lattice: L x L torus of identical site tensors T0 (legs l,u,r,d)."""
+
+    def __init__(self, T0, L, chi):
+        T0 = np.asarray(T0, dtype=np.float64)
+        if T0.ndim != 4 or len(set(T0.shape)) != 1:
+            raise ValueError("T0 must be D x D x D x D")
+        if chi < 1:
+            raise ValueError("chi >= 1")
+        self.T0, self.L, self.chi = T0, int(L), int(chi)
+        self.levels = plan(self.L)
+        self.n_levels = len(self.levels) - 1      # SVD levels: 0 .. 2m-1
+
+
+def _stochastic_chooser(seed, traj, level, tensor, chi):
+    def choose(s, n_rows):
+        uf = lambda c: philox.uniforms(seed, traj, level, tensor, c)
+        kept, st, flags, _ = truncate(s, chi, uf, n_rows)
+        return kept, st, flags
+    return choose
+
+
+def run_level(prob, k, tensors, shared, chooser_for):
+    """Split every level-k tensor and contract the plaquettes into level k+1.
+
+    Returns (new tensors, sum of ln s_1, flags, next-level shared?).
+    chooser_for(t) gives the truncation rule for tensor t.
+    """
+    lev = prob.levels[k]
+    D = tensors[0].shape[0]
+    n_rows = D * D
+    if shared:
+        # every tensor identical: the nonzero count of each matricization
+        nu = 0
+        for par in (0, 1):
+            s = svd(matricize(tensors[0], par))[1]
+            if s[0] > 0:
+                nu = max(nu, int(np.sum(s / s[0] > n_rows * 2.0 ** -52)))
+        Dn = max(1, min(prob.chi, nu))
+        exact = nu <= prob.chi
+    else:
+        Dn = min(prob.chi, n_rows)
+        exact = False
+    halves = []
+    lnacc = 0.0
+    flags = 0
+    for t in range(lev.n):
+        left, right, lns1, f = split(tensors[t], int(lev.parity[t]), Dn, chooser_for(t))
+        halves.append((left, right))
+        lnacc += lns1
+        flags |= f
+    new = []
+    for p, pa1, pa2, pa12 in lev.children_parents:
+        F3 = halves[p][1]
+        F4 = halves[pa1][1]
+        F2 = halves[pa2][0]
+        F1 = halves[pa12][0]
+        new.append(contract(F3, F4, F2, F1))
+    return new, lnacc, flags, (shared and exact)
+
+
+def run_trajectory(prob, seed, traj):
+    """One Monte Carlo trajectory -> (sign, ln|Z~|, flags)."""
+    tensors = [prob.T0] * prob.levels[0].n
+    shared = True
+    lnacc = 0.0
+    flags = 0
+    for k in range(prob.n_levels):
+        chooser_for = lambda t, k=k: _stochastic_chooser(seed, traj, k, t, prob.chi)
+        tensors, lnk, f, shared = run_level(prob, k, tensors, shared, chooser_for)
+        lnacc += lnk
+        flags |= f
+        if lnacc == -math.inf:
+            return 0, -math.inf, flags
+    T = tensors[0]
+    tr = float(np.einsum('abab->', T))
+    if tr == 0.0:
+        return 0, -math.inf, flags
+    return (1 if tr > 0 else -1), lnacc + math.log(abs(tr)), flags
+
+
+def run_many(prob, seed, first_traj, n, workers=1):
+    """Trajectories first_traj .. first_traj+n-1 -> arrays (sign, lnabs, flags).
+
+    With workers > 1 the trajectories are spread over a 'spawn' process pool;
+    each trajectory is computed exactly as in the serial loop.
+    """
+    trajs = list(range(first_traj, first_traj + n))
+    if workers <= 1 or n <= 1:
+        res = [run_trajectory(prob, seed, i) for i in trajs]
+    else:
+        import multiprocessing as mp
+        ctx = mp.get_context('spawn')
+        with ctx.Pool(workers) as pool:
+            res = pool.starmap(run_trajectory, [(prob, seed, i) for i in trajs],
+                               chunksize=max(1, n // (4 * workers)))
+    sign = np.array([r[0] for r in res], dtype=np.int8)
+    lnabs = np.array([r[1] for r in res], dtype=np.float64)
+    flags = np.array([r[2] for r in res], dtype=np.uint8)
+    return sign, lnabs, flags
