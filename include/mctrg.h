@@ -1,0 +1,174 @@
+/*
+ * mctrg.h - C ABI of the GB300 Monte Carlo TRG library.
+ *
+ * The library estimates Z = Tr(N), the trace of the partition-function
+ * tensor network of the 2D Ising model (Sec. IV, Eq. ising_model, extended by
+ * a uniform field h), by Monte Carlo tensor-network renormalization:
+ * Levin-Nave TRG (Sec. III) in which every truncated SVD keeps a random
+ * subset of chi singular values drawn with probability proportional to the
+ * product of their squares and reweighted by their inclusion probabilities
+ * (Sec. II, Eqs. Ssum, r, w, p).  Each independent trajectory coarse-grains
+ * the whole lattice, sampling every tensor independently (Sec. III), and
+ * yields an unbiased sample Z~ of Z (Sec. III, Eq. infiniteEnsemble); the
+ * sample mean and its standard error form the estimate (Sec. V, Eq.
+ * shrunkDev).
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an int status: MCTRG_OK (0) or a negative
+ *    MCTRG_E* code; mctrg_strerror() names it.  No C++ exception crosses
+ *    this boundary.
+ *  - A context owns its device memory (tensors, plans, scratch) and is not
+ *    thread-safe: one host thread at a time per context.  A server is
+ *    thread-safe.
+ *  - All device work of a context runs on the stream given in
+ *    mctrg_options.cuda_stream (NULL = the legacy default stream).
+ *  - Trajectory i of (lattice, seed) draws its uniforms from a Philox4x32-10
+ *    counter that contains first_traj + i, so it is identical whatever the
+ *    batch, chunking or co-scheduled work.
+ */
+#ifndef MCTRG_H
+#define MCTRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define MCTRG_OK            0
+#define MCTRG_EINVAL      (-1)   /* bad argument: L, chi, beta, shape, pointer */
+#define MCTRG_ENOMEM      (-2)   /* footprint exceeds the HBM budget even for one trajectory, or allocation failed */
+#define MCTRG_ENOCONV     (-3)   /* a Jacobi SVD hit the sweep cap; results returned, trajectories flagged */
+#define MCTRG_EDOMAIN     (-4)   /* sample mean of Z~ <= 0: ln Z undefined, mean_Z_scaled still valid */
+#define MCTRG_ECUDA       (-5)   /* a CUDA runtime call failed */
+#define MCTRG_ESTATE      (-6)   /* call out of order (e.g. run before init) */
+#define MCTRG_ETIMEDOUT   (-7)   /* server wait expired */
+#define MCTRG_EAGAIN      (-8)   /* server job not finished yet */
+#define MCTRG_EUNREACHABLE (-9)  /* server: target error cannot be met within max_samples */
+#define MCTRG_ENOTFOUND  (-10)   /* server: unknown job id */
+
+/* ---- per-trajectory flag bits (uint8 per trajectory) ------------------ *
+ * They mark trajectories whose kept index sets can legitimately differ
+ * between two correct implementations (near-ties).  They do not bias the
+ * estimate; they only exclude a trajectory from per-trajectory comparisons. */
+#define MCTRG_FLAG_SPLIT_CLUSTER 1u  /* kept and dropped singular values closer than 1e-8 * s_1 */
+#define MCTRG_FLAG_DRAW_TIE      2u  /* a sampler uniform fell within 1e-9 (relative) of a CDF step */
+#define MCTRG_FLAG_TINY_KEPT     4u  /* a kept singular value below 1e-7 * s_1 */
+#define MCTRG_FLAG_NOCONV       16u  /* a Jacobi SVD of this trajectory hit the sweep cap */
+
+/* ---- arithmetic of the contraction ------------------------------------ *
+ * FP64: every step in FP64.  TF32 / BF16: the plaquette contraction runs on
+ * the tensor cores with FP32 accumulation and per-tensor scaling; the SVD
+ * result and the sampling probabilities stay FP64-accurate. */
+typedef enum { MCTRG_FP64 = 0, MCTRG_TF32 = 1, MCTRG_BF16 = 2 } mctrg_precision;
+
+typedef struct {
+    int device;               /* CUDA device ordinal                                   */
+    void* cuda_stream;        /* cudaStream_t for all work of the context; NULL = default */
+    int precision;            /* mctrg_precision                                       */
+    size_t hbm_budget_bytes;  /* device memory the context may hold; 0 = 80% of free   */
+    int max_sweeps;           /* Jacobi sweep cap; 0 = 40                              */
+    int max_chunk;            /* max trajectories per device chunk; 0 = automatic      */
+} mctrg_options;
+
+/* Estimate of Z from n trajectories (Sec. III Eq. infiniteEnsemble, Sec. V Eq.
+ * shrunkDev).  With m = ln_scale = max_i ln|Z~_i| and x_i = sign_i e^{ln|Z~_i| - m}:
+ *   mean_Z_scaled = mean(x),  se_Z_scaled = std(x) / sqrt(n)   (Z^ = e^m mean(x)),
+ *   ln_mean_Z = m + ln mean(x),  se_ln_Z = se_Z_scaled / mean_Z_scaled,
+ *   ess = (sum x)^2 / sum x^2.
+ * sum_x = sum_i x_i and m2_x = sum_i (x_i - mean(x))^2, both at scale m,
+ * are the sufficient statistics that mctrg_merge_estimates combines
+ * (pairwise update of Chan, Golub and LeVeque). */
+typedef struct {
+    int64_t n;
+    double ln_mean_Z;
+    double se_ln_Z;
+    double mean_Z_scaled;
+    double se_Z_scaled;
+    double ln_scale;
+    double ess;
+    int64_t n_negative;
+    int64_t n_flagged;
+    double sum_x;
+    double m2_x;
+    int status;               /* MCTRG_OK, MCTRG_EDOMAIN or MCTRG_ENOCONV */
+} mctrg_estimate;
+
+typedef struct mctrg_ctx* mctrg_ctx_t;
+
+/* Fill *opt with defaults (device 0, default stream, FP64, automatic budget). */
+int mctrg_options_default(mctrg_options* opt);
+
+/* Create a context on opt->device.  *out receives the handle.  Errors:
+ * EINVAL (NULL pointer, bad precision), ECUDA (device unusable). */
+int mctrg_create(const mctrg_options* opt, mctrg_ctx_t* out);
+
+/* Set up an L x L periodic Ising lattice at inverse temperature beta >= 0 and
+ * field h (Sec. IV), truncating every SVD to chi kept singular values
+ * (Sec. II).  L must be a power of two, 2 <= L <= 65536; 1 <= chi <= 32.
+ * The site tensor is T[l,u,r,d] = sum_s e^{beta h s} W[s,l] W[s,u] W[s,r] W[s,d]
+ * with W[s,0] = sqrt(cosh beta), W[s,1] = s sqrt(sinh beta).  Runs the shared
+ * deterministic prefix (levels where nothing is sampled, and the one SVD of
+ * the first sampled level) on the device; blocks until it is done.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int mctrg_init_lattice(mctrg_ctx_t ctx, double beta, double h, int L, int chi);
+
+/* Same as mctrg_init_lattice with an arbitrary site tensor T0 (host pointer,
+ * D^4 doubles, index order [l][u][r][d], row-major), 1 <= D <= 8, copied. */
+int mctrg_init_tensor(mctrg_ctx_t ctx, const double* T0, int D, int L, int chi);
+
+/* Run n_samples >= 1 trajectories with counters first_traj .. first_traj+n-1
+ * (first_traj + n_samples <= 2^32) under a 64-bit seed.
+ * Outputs (caller-owned, each host or device memory, detected per pointer;
+ * NULL to skip): lnabsZ[n] = ln|Z~_i| (-inf when Z~_i = 0), sign[n] in
+ * {-1, 0, +1}, flags[n] = MCTRG_FLAG_* bits.  est (required, host) receives
+ * the estimate.  Blocks until the results are written.  Returns OK,
+ * EDOMAIN (mean <= 0), ENOCONV (some SVD hit the sweep cap), or an error. */
+int mctrg_run(mctrg_ctx_t ctx, int64_t n_samples, uint64_t seed, uint64_t first_traj,
+              double* lnabsZ, int8_t* sign, uint8_t* flags, mctrg_estimate* est);
+
+/* Device bytes the context would hold to run n_samples trajectories in the
+ * chunking it would choose (*bytes), after init.  Errors: ESTATE, EINVAL. */
+int mctrg_footprint(mctrg_ctx_t ctx, int64_t n_samples, size_t* bytes);
+
+/* Combine k >= 1 estimates of disjoint trajectory ranges of one lattice and
+ * seed into *out by rescaling their sufficient statistics to a common scale
+ * (host only; the replicas-only multi-GPU merge). */
+int mctrg_merge_estimates(const mctrg_estimate* parts, int k, mctrg_estimate* out);
+
+/* Release every resource of the context (NULL is a no-op). */
+void mctrg_destroy(mctrg_ctx_t ctx);
+
+/* Static string naming a status code. */
+const char* mctrg_strerror(int status);
+
+/* ---- serving: continuous batching of estimate jobs -------------------- *
+ * A server owns one device and a worker thread.  Jobs (beta, h, L, chi,
+ * target standard error of ln Z) arrive with mctrg_server_submit, are admitted
+ * when their device footprint fits the free budget, and advance in rounds of
+ * trajectories that share the device with every other admitted job until
+ * their target error or max_samples is reached.  Trajectory i of a job uses
+ * counter i under the job's seed, so its result is the same alone and in any
+ * mix. */
+typedef struct mctrg_server* mctrg_server_t;
+
+int mctrg_server_create(const mctrg_options* opt, mctrg_server_t* out);
+/* Non-blocking.  target_se_lnZ > 0; max_samples >= 1.  Returns EUNREACHABLE
+ * at once when the job cannot fit or its projected cost is unbounded. */
+int mctrg_server_submit(mctrg_server_t srv, double beta, double h, int L, int chi,
+                        double target_se_lnZ, int64_t max_samples, uint64_t seed,
+                        uint64_t* job_id);
+/* EAGAIN until the job is done; then fills *est and *latency_s (submit to
+ * completion, seconds) and forgets the job. */
+int mctrg_server_poll(mctrg_server_t srv, uint64_t job_id, mctrg_estimate* est, double* latency_s);
+/* Blocks up to timeout_s; ETIMEDOUT if the job is still running. */
+int mctrg_server_wait(mctrg_server_t srv, uint64_t job_id, double timeout_s,
+                      mctrg_estimate* est, double* latency_s);
+void mctrg_server_destroy(mctrg_server_t srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCTRG_H */

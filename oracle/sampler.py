@@ -36,7 +36,7 @@ import numpy as np
 FLAG_SPLIT_CLUSTER = 1   # a kept and a dropped value closer than GAP_TOL * s_1
 FLAG_DRAW_TIE = 2        # u * total within TIE_TOL * total of a CDF step
 FLAG_TINY_KEPT = 4       # a kept value below TINY_TOL * s_1
-GAP_TOL = 1e-6
+GAP_TOL = 1e-8
 TIE_TOL = 1e-9
 TINY_TOL = 1e-7
 

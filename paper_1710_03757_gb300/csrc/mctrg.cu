@@ -1,0 +1,512 @@
+// Host runtime of the MC-TRG library: contexts, the shared deterministic
+// prefix, the chunked per-trajectory level loop and the estimate.
+//
+// Trajectory pipeline (Sec. III): for the level s0 where sampling first
+// happens, every tensor of every trajectory shares one SVD (all tensors of
+// the translation-invariant network are still identical), so only the
+// sampling and the split run per (trajectory, tensor).  Every later level
+// runs, per sub-batch of (trajectory, tensor) items:
+//   form X, Yt -> GEMM (+ matricization) -> Jacobi SVD -> sample + split,
+// then adds each tensor's ln s_1 to its trajectory.  The last level's halves
+// are contracted and traced directly.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mctrg.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "mctrg_internal.h"
+
+using namespace mctrg;
+
+#define CK(call)                                     \
+  do {                                               \
+    cudaError_t e__ = (call);                        \
+    if (e__ != cudaSuccess) return fail_cuda(e__);   \
+  } while (0)
+
+namespace {
+
+int fail_cuda(cudaError_t e) {
+  set_last_cuda_error(e);
+  return MCTRG_ECUDA;
+}
+
+}  // namespace
+
+namespace mctrg {
+
+static thread_local char g_last_msg[256] = "";
+
+void set_last_cuda_error(cudaError_t e) {
+  std::snprintf(g_last_msg, sizeof(g_last_msg), "%s", cudaGetErrorString(e));
+}
+
+const char* last_message() { return g_last_msg; }
+
+cudaError_t DevBuf::ensure(size_t b) {
+  if (b <= bytes) return cudaSuccess;
+  release();
+  if (b == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&p, b);
+  if (e == cudaSuccess) bytes = b;
+  else p = nullptr;
+  return e;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+}  // namespace mctrg
+
+// ---------------------------------------------------------------------------
+extern "C" int mctrg_options_default(mctrg_options* opt) {
+  if (!opt) return MCTRG_EINVAL;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = MCTRG_FP64;
+  return MCTRG_OK;
+}
+
+extern "C" int mctrg_create(const mctrg_options* opt, mctrg_ctx_t* out) {
+  if (!opt || !out) return MCTRG_EINVAL;
+  if (opt->precision < MCTRG_FP64 || opt->precision > MCTRG_BF16) return MCTRG_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (opt->device < 0 || opt->device >= ndev) return MCTRG_EINVAL;
+  CK(cudaSetDevice(opt->device));
+  mctrg_ctx* c = new (std::nothrow) mctrg_ctx();
+  if (!c) return MCTRG_ENOMEM;
+  c->opt = *opt;
+  if (c->opt.max_sweeps <= 0) c->opt.max_sweeps = 40;
+  c->st = (cudaStream_t)opt->cuda_stream;
+  if (c->opt.hbm_budget_bytes == 0) {
+    size_t fr = 0, tot = 0;
+    cudaError_t e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) { delete c; return fail_cuda(e); }
+    c->opt.hbm_budget_bytes = (size_t)(0.8 * (double)fr);
+  }
+  *out = c;
+  return MCTRG_OK;
+}
+
+extern "C" void mctrg_destroy(mctrg_ctx_t c) {
+  if (!c) return;
+  cudaSetDevice(c->opt.device);
+  cudaStreamSynchronize(c->st);
+  c->release_all();
+  delete c;
+}
+
+extern "C" const char* mctrg_strerror(int s) {
+  switch (s) {
+    case MCTRG_OK: return "ok";
+    case MCTRG_EINVAL: return "invalid argument";
+    case MCTRG_ENOMEM: return "device memory budget exceeded or allocation failed";
+    case MCTRG_ENOCONV: return "a Jacobi SVD hit the sweep cap";
+    case MCTRG_EDOMAIN: return "sample mean of Z is not positive; ln Z undefined";
+    case MCTRG_ECUDA: return "CUDA runtime error";
+    case MCTRG_ESTATE: return "call out of order";
+    case MCTRG_ETIMEDOUT: return "timed out";
+    case MCTRG_EAGAIN: return "not finished yet";
+    case MCTRG_EUNREACHABLE: return "target error unreachable within the sample budget";
+    case MCTRG_ENOTFOUND: return "unknown job";
+    default: return "unknown status";
+  }
+}
+
+void mctrg_ctx::release_all() {
+  DevBuf* all[] = {&T0, &shM, &shW, &shSig, &shPerm, &shNnz, &shLns1, &shU, &shH, &Hbuf[0], &Hbuf[1],
+                   &Mb, &Wb, &Xb, &Yb, &sigb, &permb, &nnzb, &ilns1, &iflags, &lnacc, &tflags,
+                   &scratch, &o_lnabs, &o_sign, &o_flags, &o_tflags, &stats};
+  for (DevBuf* b : all) b->release();
+}
+
+// ---------------------------------------------------------------------------
+// Shared prefix: while every tensor of the network is identical, one A and
+// one B matricization stand for all of them.
+int mctrg_ctx::init_from_device_tensor(int D0, int L_, int chi_) {
+  ready = false;
+  L = L_;
+  chi = chi_;
+  int m = 0;
+  while ((1 << m) < L) ++m;
+  nlev = 2 * m;
+  lv.clear();
+  lnacc0 = 0.0;
+  s0 = nlev;
+  all_exact = false;
+  int D = D0;
+  // cur raw tensor lives in T0 (D^4); the plaquette result goes to shM scratch then back
+  for (int k = 0; k < nlev; ++k) {
+    const int n = D * D, np = n + (n & 1);
+    const int64_t N = level_count(L, k);
+    CK(shM.ensure(sizeof(double) * 2 * n * n));
+    CK(shW.ensure(sizeof(double) * 2 * np * n));
+    CK(shSig.ensure(sizeof(double) * 2 * np));
+    CK(shPerm.ensure(sizeof(int) * 2 * np));
+    CK(shNnz.ensure(sizeof(int) * 2));
+    CK(shLns1.ensure(sizeof(double) * 2));
+    CK(launch_matricize2(T0.as<double>(), D, shM.as<double>(), st));
+    JacobiArgs ja{};
+    ja.M = shM.as<double>(); ja.W = shW.as<double>(); ja.sig = shSig.as<double>();
+    ja.perm = shPerm.as<int>(); ja.lns1 = shLns1.as<double>(); ja.nnz = shNnz.as<int>();
+    ja.mflags = nullptr; ja.n = n; ja.n_pad = np; ja.S = 2; ja.max_sweeps = opt.max_sweeps;
+    CK(launch_jacobi(ja, st));
+    int hn[2];
+    double hl[2];
+    CK(cudaMemcpyAsync(hn, shNnz.p, sizeof(hn), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hl, shLns1.p, sizeof(hl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    lnacc0 += (double)(N / 2) * (hl[0] + hl[1]);
+    const int nu = std::max(hn[0], hn[1]);
+    const int kc = std::max(1, std::min(chi, nu));
+    LevelInfo li{N, D, n, np, kc};
+    lv.push_back(li);
+    if (nu <= chi) {
+      // exact level: keep every nonzero value of both matricizations
+      CK(shH.ensure(sizeof(double) * 2 * (2 * (size_t)n * kc)));
+      CK(scratch.ensure(sizeof(double) * sample_scratch_doubles(n, chi, 2)));
+      SampleArgs sa{};
+      sa.M = shM.as<double>(); sa.W = shW.as<double>(); sa.sig = shSig.as<double>();
+      sa.perm = shPerm.as<int>(); sa.nnz = shNnz.as<int>(); sa.Urows = nullptr;
+      sa.n = n; sa.n_pad = np; sa.chi = chi; sa.kc = kc; sa.stochastic = 0; sa.shared_svd = 0;
+      sa.item0 = 0; sa.n_items = 2; sa.N = 2; sa.L = L; sa.level = k; sa.seed = 0; sa.traj0 = 0;
+      sa.H = shH.as<double>(); sa.h_item0 = 0; sa.iflags = nullptr; sa.scratch = scratch.as<double>();
+      CK(launch_sample_split(sa, st, 2));
+      CK(Xb.ensure(sizeof(double) * (size_t)kc * kc * n));
+      CK(Yb.ensure(sizeof(double) * (size_t)kc * kc * n));
+      XYArgs xa{};
+      xa.H = shH.as<double>(); xa.h_item0 = 0; xa.d = D; xa.D = kc; xa.c0 = 0; xa.n_items = 1;
+      xa.Nnew = 1; xa.Nold = 2; xa.L = L; xa.level_old = k; xa.fixed_parents = 1;
+      xa.X = Xb.as<double>(); xa.Yt = Yb.as<double>();
+      CK(launch_form_xy(xa, st));
+      if (k == nlev - 1) {
+        CK(o_lnabs.ensure(sizeof(double)));
+        CK(o_sign.ensure(1));
+        CK(launch_trace(Xb.as<double>(), Yb.as<double>(), (int64_t)kc * kc * n, 1, lnacc0, nullptr,
+                        o_lnabs.as<double>(), o_sign.as<int8_t>(), st));
+        int8_t sg = 0;
+        CK(cudaMemcpyAsync(&const_lnabs, o_lnabs.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&sg, o_sign.p, 1, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const_sign = sg;
+        all_exact = true;
+        break;
+      }
+      const size_t tbytes = sizeof(double) * (size_t)kc * kc * kc * kc;
+      CK(Mb.ensure(tbytes));
+      GemmArgs gm{};
+      gm.X = Xb.as<double>(); gm.Yt = Yb.as<double>(); gm.M = Mb.as<double>(); gm.D = kc; gm.K = n;
+      gm.c0 = 0; gm.n_items = 1; gm.Nnew = 1; gm.L = L; gm.level_new = k + 1; gm.fixed_parity = 0;
+      CK(launch_gemm_f64(gm, st));
+      CK(T0.ensure(tbytes));
+      CK(cudaMemcpyAsync(T0.p, Mb.p, tbytes, cudaMemcpyDeviceToDevice, st));
+      D = kc;
+      continue;
+    }
+    // first stochastic level: keep its shared SVD for the per-trajectory draws
+    s0 = k;
+    CK(shU.ensure(sizeof(double) * 2 * (size_t)np * n));
+    CK(launch_u_rows(shM.as<double>(), shW.as<double>(), shSig.as<double>(), shPerm.as<int>(),
+                     shNnz.as<int>(), shU.as<double>(), n, np, 2, st));
+    break;
+  }
+  if (!all_exact) {
+    for (int k = s0 + 1; k < nlev; ++k) {
+      const int D2 = lv[k - 1].kc, n = D2 * D2, np = n + (n & 1);
+      lv.push_back(LevelInfo{level_count(L, k), D2, n, np, std::min(chi, n)});
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  ready = true;
+  return MCTRG_OK;
+}
+
+static bool is_pow2(int L) { return L >= 2 && (L & (L - 1)) == 0; }
+
+extern "C" int mctrg_init_lattice(mctrg_ctx_t c, double beta, double h, int L, int chi) {
+  if (!c) return MCTRG_EINVAL;
+  if (!is_pow2(L) || L > 65536 || chi < 1 || chi > 32 || !(beta >= 0.0) || !std::isfinite(beta) ||
+      !std::isfinite(h))
+    return MCTRG_EINVAL;
+  CK(cudaSetDevice(c->opt.device));
+  CK(c->T0.ensure(16 * sizeof(double)));
+  CK(launch_site_tensor(beta, h, c->T0.as<double>(), c->st));
+  return c->init_from_device_tensor(2, L, chi);
+}
+
+extern "C" int mctrg_init_tensor(mctrg_ctx_t c, const double* T0, int D, int L, int chi) {
+  if (!c || !T0) return MCTRG_EINVAL;
+  if (!is_pow2(L) || L > 65536 || chi < 1 || chi > 32 || D < 1 || D > 8) return MCTRG_EINVAL;
+  CK(cudaSetDevice(c->opt.device));
+  const size_t bytes = sizeof(double) * (size_t)D * D * D * D;
+  CK(c->T0.ensure(bytes));
+  CK(cudaMemcpyAsync(c->T0.p, T0, bytes, cudaMemcpyHostToDevice, c->st));
+  return c->init_from_device_tensor(D, L, chi);
+}
+
+// ---------------------------------------------------------------------------
+// Memory plan: bytes per trajectory of a chunk, and bytes per in-flight item.
+void mctrg_ctx::plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& total) const {
+  size_t per_traj = 2 * sizeof(double) + sizeof(uint32_t);   // lnacc, tflags
+  size_t max_pair = 0, max_items = 0, per_item = 0;
+  for (int k = s0; k < nlev; ++k) {
+    const LevelInfo& a = lv[k];
+    size_t hk = (size_t)a.N * 2 * a.n * a.kc * sizeof(double);
+    size_t hp = (k > s0) ? (size_t)lv[k - 1].N * 2 * lv[k - 1].n * lv[k - 1].kc * sizeof(double) : 0;
+    max_pair = std::max(max_pair, hk + hp);
+    max_items = std::max(max_items, (size_t)a.N);
+    if (k > s0) {
+      const size_t d2 = (size_t)lv[k - 1].D * lv[k - 1].D;
+      size_t pi = (2 * (size_t)a.n * d2 + (size_t)a.n * a.n + (size_t)a.n_pad * a.n + a.n_pad) * sizeof(double) +
+                  (a.n_pad + 1) * sizeof(int) + sizeof(double) + sizeof(uint32_t);
+      per_item = std::max(per_item, pi);
+    }
+  }
+  {  // final contraction X, Yt per trajectory
+    const LevelInfo& a = lv[nlev - 1];
+    size_t fin = 2 * (size_t)a.kc * a.kc * a.n * sizeof(double);
+    per_traj += fin;
+  }
+  per_traj += max_pair + max_items * (sizeof(double) + sizeof(uint32_t));
+  const size_t budget = opt.hbm_budget_bytes;
+  const size_t work_budget = std::max<size_t>(budget / 4, 1);
+  S = per_item ? (int64_t)std::max<size_t>(1, std::min<size_t>(work_budget / per_item, 1 << 16)) : 1;
+  const size_t work = per_item * (size_t)S + sample_scratch_doubles(lv[nlev - 1].n, chi, 1024) * sizeof(double);
+  const size_t rest = budget > work ? budget - work : 0;
+  B = (int64_t)(rest / std::max<size_t>(per_traj, 1));
+  if (opt.max_chunk > 0) B = std::min<int64_t>(B, opt.max_chunk);
+  B = std::min<int64_t>(B, n_samples);
+  total = work + (size_t)std::max<int64_t>(B, 1) * per_traj + (size_t)n_samples * 14;
+}
+
+extern "C" int mctrg_footprint(mctrg_ctx_t c, int64_t n_samples, size_t* bytes) {
+  if (!c || !bytes || n_samples < 1) return MCTRG_EINVAL;
+  if (!c->ready) return MCTRG_ESTATE;
+  if (c->all_exact) { *bytes = (size_t)n_samples * 14; return MCTRG_OK; }
+  int64_t B, S;
+  c->plan_chunks(n_samples, B, S, *bytes);
+  return B >= 1 ? MCTRG_OK : MCTRG_ENOMEM;
+}
+
+static void finalize_estimate(const double* s, int64_t n, mctrg_estimate* est) {
+  std::memset(est, 0, sizeof(*est));
+  est->n = n;
+  est->ln_scale = s[0];
+  est->sum_x = s[1];
+  est->m2_x = s[2];
+  est->n_negative = (int64_t)s[3];
+  est->n_flagged = (int64_t)s[4];
+  finish_estimate(est);
+}
+
+namespace mctrg {
+void finish_estimate(mctrg_estimate* e) {
+  const double n = (double)e->n;
+  const double mean = e->sum_x / n;
+  e->mean_Z_scaled = mean;
+  e->se_Z_scaled = e->n > 1 ? std::sqrt(std::max(0.0, e->m2_x / (n - 1.0)) / n) : NAN;
+  const double sumsq = e->m2_x + n * mean * mean;
+  e->ess = sumsq > 0 ? e->sum_x * e->sum_x / sumsq : 0.0;
+  if (mean > 0) {
+    e->ln_mean_Z = e->ln_scale + std::log(mean);
+    e->se_ln_Z = e->se_Z_scaled / mean;
+    e->status = MCTRG_OK;
+  } else {
+    e->ln_mean_Z = NAN;
+    e->se_ln_Z = NAN;
+    e->status = MCTRG_EDOMAIN;
+  }
+}
+}  // namespace mctrg
+
+int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_out, int8_t* sign_out,
+                   uint8_t* flags_out, mctrg_estimate* est) {
+  CK(o_lnabs.ensure(sizeof(double) * n));
+  CK(o_sign.ensure((size_t)n));
+  CK(o_flags.ensure((size_t)n));
+  CK(stats.ensure(8 * sizeof(double)));
+  if (all_exact) {
+    std::vector<double> hl((size_t)n, const_lnabs);
+    std::vector<int8_t> hs((size_t)n, (int8_t)const_sign);
+    CK(cudaMemcpyAsync(o_lnabs.p, hl.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(o_sign.p, hs.data(), (size_t)n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(o_flags.p, 0, (size_t)n, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    int64_t B, S;
+    size_t total;
+    plan_chunks(n, B, S, total);
+    if (B < 1) return MCTRG_ENOMEM;
+    CK(o_tflags.ensure(sizeof(uint32_t) * (size_t)B));
+    CK(lnacc.ensure(sizeof(double) * (size_t)B));
+    const int grid_s = 1024;
+    size_t max_h = 0, max_items = 0, max_xy = 0, max_m = 0, max_w = 0, max_np = 0, max_scr = 0;
+    for (int k = s0; k < nlev; ++k) {
+      const LevelInfo& a = lv[k];
+      max_h = std::max(max_h, (size_t)B * a.N * 2 * a.n * a.kc);
+      max_items = std::max(max_items, (size_t)B * a.N);
+      max_scr = std::max(max_scr, sample_scratch_doubles(a.n, chi, grid_s));
+      if (k > s0) {
+        const size_t d2 = (size_t)lv[k - 1].D * lv[k - 1].D;
+        max_xy = std::max(max_xy, (size_t)S * a.n * d2);
+        max_m = std::max(max_m, (size_t)S * a.n * a.n);
+        max_w = std::max(max_w, (size_t)S * a.n_pad * a.n);
+        max_np = std::max(max_np, (size_t)S * a.n_pad);
+      }
+    }
+    {
+      const LevelInfo& a = lv[nlev - 1];
+      max_xy = std::max(max_xy, (size_t)B * a.kc * a.kc * a.n);
+    }
+    CK(Hbuf[0].ensure(sizeof(double) * max_h));
+    CK(Hbuf[1].ensure(sizeof(double) * max_h));
+    CK(iflags.ensure(sizeof(uint32_t) * max_items));
+    CK(ilns1.ensure(sizeof(double) * max_items));
+    CK(Xb.ensure(sizeof(double) * std::max<size_t>(max_xy, 1)));
+    CK(Yb.ensure(sizeof(double) * std::max<size_t>(max_xy, 1)));
+    CK(Mb.ensure(sizeof(double) * std::max<size_t>(max_m, 1)));
+    CK(Wb.ensure(sizeof(double) * std::max<size_t>(max_w, 1)));
+    CK(sigb.ensure(sizeof(double) * std::max<size_t>(max_np, 1)));
+    CK(permb.ensure(sizeof(int) * std::max<size_t>(max_np, 1)));
+    CK(nnzb.ensure(sizeof(int) * std::max<int64_t>(S, 1)));
+    CK(scratch.ensure(sizeof(double) * max_scr));
+    for (int64_t c0 = 0; c0 < n; c0 += B) {
+      const int64_t Bc = std::min(B, n - c0);
+      const uint64_t traj0 = first_traj + (uint64_t)c0;
+      CK(cudaMemsetAsync(lnacc.p, 0, sizeof(double) * Bc, st));
+      CK(cudaMemsetAsync(o_tflags.p, 0, sizeof(uint32_t) * Bc, st));
+      int cur = 0;
+      {  // level s0: shared SVD, per-(trajectory, tensor) sampling
+        const LevelInfo& a = lv[s0];
+        const int64_t items = Bc * a.N;
+        CK(cudaMemsetAsync(iflags.p, 0, sizeof(uint32_t) * items, st));
+        SampleArgs sa{};
+        sa.M = shM.as<double>(); sa.W = shW.as<double>(); sa.sig = shSig.as<double>();
+        sa.perm = shPerm.as<int>(); sa.nnz = shNnz.as<int>(); sa.Urows = shU.as<double>();
+        sa.n = a.n; sa.n_pad = a.n_pad; sa.chi = chi; sa.kc = a.kc; sa.stochastic = 1; sa.shared_svd = 1;
+        sa.item0 = 0; sa.n_items = items; sa.N = a.N; sa.L = L; sa.level = s0; sa.seed = seed;
+        sa.traj0 = traj0; sa.H = Hbuf[cur].as<double>(); sa.h_item0 = 0; sa.iflags = iflags.as<uint32_t>();
+        sa.scratch = scratch.as<double>();
+        CK(launch_sample_split(sa, st, grid_s));
+        CK(launch_traj_accum(nullptr, iflags.as<uint32_t>(), a.N, Bc, lnacc.as<double>(),
+                             o_tflags.as<uint32_t>(), st));
+      }
+      for (int k = s0 + 1; k < nlev; ++k) {
+        const LevelInfo& a = lv[k];
+        const LevelInfo& p = lv[k - 1];
+        const int prev = cur;
+        cur ^= 1;
+        const int64_t items = Bc * a.N;
+        CK(cudaMemsetAsync(iflags.p, 0, sizeof(uint32_t) * items, st));
+        for (int64_t i0 = 0; i0 < items; i0 += S) {
+          const int64_t Si = std::min(S, items - i0);
+          XYArgs xa{};
+          xa.H = Hbuf[prev].as<double>(); xa.h_item0 = 0; xa.d = p.D; xa.D = p.kc; xa.c0 = i0;
+          xa.n_items = Si; xa.Nnew = a.N; xa.Nold = p.N; xa.L = L; xa.level_old = k - 1;
+          xa.fixed_parents = 0; xa.X = Xb.as<double>(); xa.Yt = Yb.as<double>();
+          CK(launch_form_xy(xa, st));
+          GemmArgs gm{};
+          gm.X = Xb.as<double>(); gm.Yt = Yb.as<double>(); gm.M = Mb.as<double>(); gm.D = a.D;
+          gm.K = p.D * p.D; gm.c0 = i0; gm.n_items = Si; gm.Nnew = a.N; gm.L = L; gm.level_new = k;
+          gm.fixed_parity = -1;
+          CK(launch_gemm_f64(gm, st));
+          JacobiArgs ja{};
+          ja.M = Mb.as<double>(); ja.W = Wb.as<double>(); ja.sig = sigb.as<double>();
+          ja.perm = permb.as<int>(); ja.lns1 = ilns1.as<double>() + i0; ja.nnz = nnzb.as<int>();
+          ja.mflags = iflags.as<uint32_t>() + i0; ja.n = a.n; ja.n_pad = a.n_pad; ja.S = (int)Si;
+          ja.max_sweeps = opt.max_sweeps;
+          CK(launch_jacobi(ja, st));
+          SampleArgs sa{};
+          sa.M = Mb.as<double>(); sa.W = Wb.as<double>(); sa.sig = sigb.as<double>();
+          sa.perm = permb.as<int>(); sa.nnz = nnzb.as<int>(); sa.Urows = nullptr;
+          sa.n = a.n; sa.n_pad = a.n_pad; sa.chi = chi; sa.kc = a.kc; sa.stochastic = 1; sa.shared_svd = 0;
+          sa.item0 = i0; sa.n_items = Si; sa.N = a.N; sa.L = L; sa.level = k; sa.seed = seed;
+          sa.traj0 = traj0; sa.H = Hbuf[cur].as<double>(); sa.h_item0 = 0;
+          sa.iflags = iflags.as<uint32_t>(); sa.scratch = scratch.as<double>();
+          CK(launch_sample_split(sa, st, grid_s));
+        }
+        CK(launch_traj_accum(ilns1.as<double>(), iflags.as<uint32_t>(), a.N, Bc, lnacc.as<double>(),
+                             o_tflags.as<uint32_t>(), st));
+      }
+      {  // final contraction and trace
+        const LevelInfo& p = lv[nlev - 1];
+        XYArgs xa{};
+        xa.H = Hbuf[cur].as<double>(); xa.h_item0 = 0; xa.d = p.D; xa.D = p.kc; xa.c0 = 0;
+        xa.n_items = Bc; xa.Nnew = 1; xa.Nold = p.N; xa.L = L; xa.level_old = nlev - 1;
+        xa.fixed_parents = 0; xa.X = Xb.as<double>(); xa.Yt = Yb.as<double>();
+        CK(launch_form_xy(xa, st));
+        CK(launch_trace(Xb.as<double>(), Yb.as<double>(), (int64_t)p.kc * p.kc * p.n, Bc, lnacc0,
+                        lnacc.as<double>(), o_lnabs.as<double>() + c0, o_sign.as<int8_t>() + c0, st));
+        CK(launch_flags_to_u8(o_tflags.as<uint32_t>(), o_flags.as<uint8_t>() + c0, Bc, st));
+      }
+    }
+  }
+  CK(launch_estimate(o_lnabs.as<double>(), o_sign.as<int8_t>(), o_flags.as<uint8_t>(), n,
+                     stats.as<double>(), st));
+  double hs[6];
+  CK(cudaMemcpyAsync(hs, stats.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  if (lnabs_out) CK(cudaMemcpyAsync(lnabs_out, o_lnabs.p, sizeof(double) * n, cudaMemcpyDefault, st));
+  if (sign_out) CK(cudaMemcpyAsync(sign_out, o_sign.p, (size_t)n, cudaMemcpyDefault, st));
+  if (flags_out) CK(cudaMemcpyAsync(flags_out, o_flags.p, (size_t)n, cudaMemcpyDefault, st));
+  CK(cudaStreamSynchronize(st));
+  finalize_estimate(hs, n, est);
+  // any trajectory whose SVD hit the sweep cap
+  if (est->status == MCTRG_OK && any_noconv(n)) est->status = MCTRG_ENOCONV;
+  return est->status == MCTRG_EDOMAIN ? MCTRG_EDOMAIN : est->status;
+}
+
+bool mctrg_ctx::any_noconv(int64_t n) {
+  std::vector<uint8_t> f((size_t)n);
+  if (cudaMemcpy(f.data(), o_flags.p, (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+  for (uint8_t v : f)
+    if (v & FLAG_NOCONV) return true;
+  return false;
+}
+
+extern "C" int mctrg_run(mctrg_ctx_t c, int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs,
+                         int8_t* sign, uint8_t* flags, mctrg_estimate* est) {
+  if (!c || !est || n < 1) return MCTRG_EINVAL;
+  if (first_traj + (uint64_t)n > (1ull << 32)) return MCTRG_EINVAL;
+  if (!c->ready) return MCTRG_ESTATE;
+  CK(cudaSetDevice(c->opt.device));
+  return c->run(n, seed, first_traj, lnabs, sign, flags, est);
+}
+
+extern "C" int mctrg_merge_estimates(const mctrg_estimate* parts, int k, mctrg_estimate* out) {
+  if (!parts || !out || k < 1) return MCTRG_EINVAL;
+  double m = -INFINITY;
+  int64_t n = 0, nneg = 0, nflag = 0;
+  for (int i = 0; i < k; ++i) {
+    if (parts[i].n < 1) return MCTRG_EINVAL;
+    m = std::max(m, parts[i].ln_scale);
+    n += parts[i].n;
+    nneg += parts[i].n_negative;
+    nflag += parts[i].n_flagged;
+  }
+  double sum = 0.0;
+  for (int i = 0; i < k; ++i) sum += parts[i].sum_x * std::exp(parts[i].ln_scale - m);
+  const double mean = sum / (double)n;
+  double m2 = 0.0;
+  for (int i = 0; i < k; ++i) {
+    const double f = std::exp(parts[i].ln_scale - m);
+    const double mi = parts[i].sum_x * f / (double)parts[i].n;
+    m2 += parts[i].m2_x * f * f + (double)parts[i].n * (mi - mean) * (mi - mean);
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->n = n;
+  out->ln_scale = m;
+  out->sum_x = sum;
+  out->m2_x = m2;
+  out->n_negative = nneg;
+  out->n_flagged = nflag;
+  finish_estimate(out);
+  return MCTRG_OK;
+}

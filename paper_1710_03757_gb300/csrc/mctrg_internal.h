@@ -1,0 +1,57 @@
+// Internal host-side state of an MC-TRG context.
+#pragma once
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mctrg.h"
+
+namespace mctrg {
+
+// A device allocation that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t b);
+  void release();
+  template <class T> T* as() const { return (T*)p; }
+};
+
+// Shape of one SVD level k: N tensors per trajectory with legs of dimension
+// D, matricized as n x n (n = D^2, n_pad = n rounded up to even), split with
+// kc kept columns (the leg dimension of level k+1).
+struct LevelInfo {
+  int64_t N;
+  int D, n, n_pad, kc;
+};
+
+void set_last_cuda_error(cudaError_t e);
+const char* last_message();
+void finish_estimate(mctrg_estimate* e);
+
+}  // namespace mctrg
+
+struct mctrg_ctx {
+  mctrg_options opt{};
+  cudaStream_t st = nullptr;
+  bool ready = false;
+  int L = 0, chi = 0, nlev = 0;
+  std::vector<mctrg::LevelInfo> lv;
+  int s0 = 0;               // first level where sampling happens (nlev: none)
+  double lnacc0 = 0.0;      // sum of ln s_1 over the shared levels 0..s0
+  bool all_exact = false;
+  double const_lnabs = 0.0;
+  int const_sign = 0;
+  mctrg::DevBuf T0, shM, shW, shSig, shPerm, shNnz, shLns1, shU, shH;
+  mctrg::DevBuf Hbuf[2], Mb, Wb, Xb, Yb, sigb, permb, nnzb, ilns1, iflags, lnacc, tflags, scratch;
+  mctrg::DevBuf o_lnabs, o_sign, o_flags, o_tflags, stats;
+
+  int init_from_device_tensor(int D0, int L, int chi);
+  void plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& total) const;
+  int run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs, int8_t* sign, uint8_t* flags,
+          mctrg_estimate* est);
+  bool any_noconv(int64_t n);
+  void release_all();
+};

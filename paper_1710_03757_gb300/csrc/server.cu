@@ -1,0 +1,253 @@
+// Serving loop: continuous batching of Monte Carlo TRG estimate jobs.
+//
+// Jobs (beta, h, L, chi, target standard error of ln Z) arrive at any time.
+// An admission thread admits queued jobs in arrival order whenever their
+// device footprint fits the memory not held by running jobs; each admitted
+// job then advances in rounds of trajectories on its own context and CUDA
+// stream, so the kernels of all running jobs share the device concurrently,
+// and a finished job frees its memory for the next queued one.  A job's
+// trajectory i always uses Philox counter i under the job's seed and its
+// rounds merge through the sufficient statistics of mctrg_merge_estimates,
+// so its result is the same alone and in any mix.
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+#include "../../include/mctrg.h"
+#include "mctrg_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+  uint64_t id = 0;
+  double beta = 0, h = 0, target = 0;
+  int L = 0, chi = 0;
+  int64_t max_samples = 0;
+  uint64_t seed = 0;
+  size_t footprint = 0;
+  Clock::time_point t_submit, t_done;
+  int state = 0;            // 0 queued, 1 running, 2 done
+  int status = MCTRG_OK;
+  mctrg_estimate est{};
+  std::thread th;
+};
+
+// Upper bound of the device bytes of a job that runs rounds of R trajectories:
+// leg dimensions grow as D' = min(chi, D^2) from D = 2.
+size_t job_footprint(int L, int chi, int64_t R) {
+  int m = 0;
+  while ((1 << m) < L) ++m;
+  const int nlev = 2 * m;
+  int D = 2;
+  size_t per_traj = 64, work = 0, maxpair = 0, prevh = 0;
+  for (int k = 0; k < nlev; ++k) {
+    const size_t n = (size_t)D * D;
+    const int kc = (int)std::min<size_t>((size_t)chi, n);
+    const size_t N = ((size_t)L * L) >> k;
+    const size_t hk = N * 2 * n * kc * 8;
+    maxpair = std::max(maxpair, hk + prevh);
+    prevh = hk;
+    work = std::max(work, (size_t)(5 * n * n * 8));
+    D = kc;
+  }
+  per_traj += maxpair;
+  return per_traj * (size_t)R + work * 4096 + (64u << 20);
+}
+
+}  // namespace
+
+struct mctrg_server {
+  mctrg_options opt{};
+  size_t budget = 0, used = 0;
+  int max_active = 64;
+  std::mutex mu;
+  std::condition_variable cv;       // admission thread wakes on submit / finish / stop
+  std::condition_variable done_cv;  // waiters wake when a job finishes
+  std::deque<Job*> queue;
+  std::map<uint64_t, Job*> jobs;
+  int active = 0;
+  bool stop = false;
+  uint64_t next_id = 1;
+  std::thread admitter;
+
+  static constexpr int64_t kRound0 = 256;   // first round; later rounds double up to kRoundMax
+  static constexpr int64_t kRoundMax = 8192;
+
+  void run_job(Job* j) {
+    cudaSetDevice(opt.device);
+    cudaStream_t st = nullptr;
+    int status = MCTRG_OK;
+    mctrg_estimate total{};
+    bool have = false;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) status = MCTRG_ECUDA;
+    mctrg_ctx_t ctx = nullptr;
+    if (status == MCTRG_OK) {
+      mctrg_options o = opt;
+      o.cuda_stream = st;
+      o.hbm_budget_bytes = j->footprint;
+      status = mctrg_create(&o, &ctx);
+    }
+    if (status == MCTRG_OK) status = mctrg_init_lattice(ctx, j->beta, j->h, j->L, j->chi);
+    int64_t done = 0, round = kRound0;
+    while (status == MCTRG_OK && done < j->max_samples) {
+      const int64_t R = std::min(round, j->max_samples - done);
+      mctrg_estimate e{};
+      int s = mctrg_run(ctx, R, j->seed, (uint64_t)done, nullptr, nullptr, nullptr, &e);
+      if (s != MCTRG_OK && s != MCTRG_EDOMAIN && s != MCTRG_ENOCONV) { status = s; break; }
+      if (!have) { total = e; have = true; }
+      else {
+        mctrg_estimate parts[2] = {total, e};
+        mctrg_merge_estimates(parts, 2, &total);
+      }
+      done += R;
+      if (total.status == MCTRG_OK && total.se_ln_Z <= j->target) break;
+      round = std::min(round * 2, kRoundMax);
+    }
+    if (status == MCTRG_OK && !(total.status == MCTRG_OK && total.se_ln_Z <= j->target))
+      status = MCTRG_EUNREACHABLE;
+    if (ctx) mctrg_destroy(ctx);
+    if (st) cudaStreamDestroy(st);
+    std::lock_guard<std::mutex> lk(mu);
+    j->est = total;
+    j->status = status;
+    j->t_done = Clock::now();
+    j->state = 2;
+    used -= j->footprint;
+    --active;
+    cv.notify_all();
+    done_cv.notify_all();
+  }
+
+  void admission_loop() {
+    std::unique_lock<std::mutex> lk(mu);
+    while (!stop) {
+      bool admitted = false;
+      while (!queue.empty() && active < max_active && used + queue.front()->footprint <= budget) {
+        Job* j = queue.front();
+        queue.pop_front();
+        used += j->footprint;
+        ++active;
+        j->state = 1;
+        j->th = std::thread(&mctrg_server::run_job, this, j);
+        admitted = true;
+      }
+      if (!admitted) cv.wait(lk);
+    }
+  }
+};
+
+extern "C" int mctrg_server_create(const mctrg_options* opt, mctrg_server_t* out) {
+  if (!opt || !out) return MCTRG_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) return MCTRG_ECUDA;
+  if (opt->device < 0 || opt->device >= ndev) return MCTRG_EINVAL;
+  if (cudaSetDevice(opt->device) != cudaSuccess) return MCTRG_ECUDA;
+  mctrg_server* s = new mctrg_server();
+  s->opt = *opt;
+  if (s->opt.hbm_budget_bytes == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { delete s; return MCTRG_ECUDA; }
+    s->opt.hbm_budget_bytes = (size_t)(0.8 * (double)fr);
+  }
+  s->budget = s->opt.hbm_budget_bytes;
+  s->admitter = std::thread(&mctrg_server::admission_loop, s);
+  *out = s;
+  return MCTRG_OK;
+}
+
+extern "C" int mctrg_server_submit(mctrg_server_t s, double beta, double h, int L, int chi,
+                                   double target_se_lnZ, int64_t max_samples, uint64_t seed,
+                                   uint64_t* job_id) {
+  if (!s || !job_id) return MCTRG_EINVAL;
+  if (L < 2 || (L & (L - 1)) || L > 65536 || chi < 1 || chi > 32 || !(beta >= 0) ||
+      !std::isfinite(beta) || !std::isfinite(h) || !(target_se_lnZ > 0) || max_samples < 1 ||
+      (uint64_t)max_samples > (1ull << 32))
+    return MCTRG_EINVAL;
+  Job* j = new Job();
+  j->beta = beta; j->h = h; j->L = L; j->chi = chi; j->target = target_se_lnZ;
+  j->max_samples = max_samples; j->seed = seed;
+  j->footprint = job_footprint(L, chi, std::min<int64_t>(max_samples, mctrg_server::kRoundMax));
+  if (j->footprint > s->budget) {   // can never be admitted
+    delete j;
+    return MCTRG_EUNREACHABLE;
+  }
+  j->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lk(s->mu);
+  j->id = s->next_id++;
+  s->jobs[j->id] = j;
+  s->queue.push_back(j);
+  *job_id = j->id;
+  s->cv.notify_all();
+  return MCTRG_OK;
+}
+
+static int take_result(mctrg_server* s, std::map<uint64_t, Job*>::iterator it, mctrg_estimate* est,
+                       double* latency_s) {
+  Job* j = it->second;
+  if (est) *est = j->est;
+  if (latency_s) *latency_s = std::chrono::duration<double>(j->t_done - j->t_submit).count();
+  const int st = j->status;
+  s->jobs.erase(it);
+  if (j->th.joinable()) j->th.join();
+  delete j;
+  return st;
+}
+
+extern "C" int mctrg_server_poll(mctrg_server_t s, uint64_t job_id, mctrg_estimate* est, double* latency_s) {
+  if (!s) return MCTRG_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return MCTRG_ENOTFOUND;
+  if (it->second->state != 2) return MCTRG_EAGAIN;
+  return take_result(s, it, est, latency_s);
+}
+
+extern "C" int mctrg_server_wait(mctrg_server_t s, uint64_t job_id, double timeout_s, mctrg_estimate* est,
+                                 double* latency_s) {
+  if (!s) return MCTRG_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                           std::chrono::duration<double>(std::max(0.0, timeout_s)));
+  for (;;) {
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return MCTRG_ENOTFOUND;
+    if (it->second->state == 2) return take_result(s, it, est, latency_s);
+    if (s->done_cv.wait_until(lk, deadline) == std::cv_status::timeout) {
+      it = s->jobs.find(job_id);
+      if (it != s->jobs.end() && it->second->state == 2) return take_result(s, it, est, latency_s);
+      return MCTRG_ETIMEDOUT;
+    }
+  }
+}
+
+extern "C" void mctrg_server_destroy(mctrg_server_t s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    // queued jobs never start
+    for (Job* j : s->queue) { s->jobs.erase(j->id); delete j; }
+    s->queue.clear();
+    s->cv.notify_all();
+  }
+  if (s->admitter.joinable()) s->admitter.join();
+  std::map<uint64_t, Job*> rest;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    rest.swap(s->jobs);
+  }
+  for (auto& kv : rest) {
+    if (kv.second->th.joinable()) kv.second->th.join();
+    delete kv.second;
+  }
+  delete s;
+}

@@ -1,0 +1,217 @@
+"""Thin ctypes binding of the MC-TRG C ABI (include/mctrg.h, include/mctrg_host.h).
+
+Argument marshalling only: every step of the method runs in libmctrg.so.
+Names follow the C functions.  Output buffers may be numpy arrays (host) or
+torch tensors (host or device); the library detects device pointers itself.
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libmctrg.so")
+
+MCTRG_OK, MCTRG_EINVAL, MCTRG_ENOMEM, MCTRG_ENOCONV, MCTRG_EDOMAIN = 0, -1, -2, -3, -4
+MCTRG_ECUDA, MCTRG_ESTATE, MCTRG_ETIMEDOUT, MCTRG_EAGAIN, MCTRG_EUNREACHABLE = -5, -6, -7, -8, -9
+MCTRG_ENOTFOUND = -10
+MCTRG_FP64, MCTRG_TF32, MCTRG_BF16 = 0, 1, 2
+FLAG_SPLIT_CLUSTER, FLAG_DRAW_TIE, FLAG_TINY_KEPT, FLAG_NOCONV = 1, 2, 4, 16
+
+# every symbol the headers declare (checked by the CPU test suite)
+EXPORTS = [
+    "mctrg_options_default", "mctrg_create", "mctrg_init_lattice", "mctrg_init_tensor",
+    "mctrg_run", "mctrg_footprint", "mctrg_merge_estimates", "mctrg_destroy", "mctrg_strerror",
+    "mctrg_server_create", "mctrg_server_submit", "mctrg_server_poll", "mctrg_server_wait",
+    "mctrg_server_destroy", "mctrg_plan_level", "mctrg_philox_uniform",
+]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_size_t), ("max_sweeps", ctypes.c_int),
+                ("max_chunk", ctypes.c_int)]
+
+
+class Estimate(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("ln_mean_Z", ctypes.c_double), ("se_ln_Z", ctypes.c_double),
+                ("mean_Z_scaled", ctypes.c_double), ("se_Z_scaled", ctypes.c_double),
+                ("ln_scale", ctypes.c_double), ("ess", ctypes.c_double), ("n_negative", ctypes.c_int64),
+                ("n_flagged", ctypes.c_int64), ("sum_x", ctypes.c_double), ("m2_x", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmctrg.so is not built (%s): run "
+                               "`python -m paper_1710_03757_gb300.build`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        c_int, c_double, vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+        i64, u64, u32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32
+        sig = {
+            "mctrg_options_default": (c_int, [ctypes.POINTER(Options)]),
+            "mctrg_create": (c_int, [ctypes.POINTER(Options), ctypes.POINTER(vp)]),
+            "mctrg_init_lattice": (c_int, [vp, c_double, c_double, c_int, c_int]),
+            "mctrg_init_tensor": (c_int, [vp, vp, c_int, c_int, c_int]),
+            "mctrg_run": (c_int, [vp, i64, u64, u64, vp, vp, vp, ctypes.POINTER(Estimate)]),
+            "mctrg_footprint": (c_int, [vp, i64, ctypes.POINTER(ctypes.c_size_t)]),
+            "mctrg_merge_estimates": (c_int, [ctypes.POINTER(Estimate), c_int, ctypes.POINTER(Estimate)]),
+            "mctrg_destroy": (None, [vp]),
+            "mctrg_strerror": (ctypes.c_char_p, [c_int]),
+            "mctrg_server_create": (c_int, [ctypes.POINTER(Options), ctypes.POINTER(vp)]),
+            "mctrg_server_submit": (c_int, [vp, c_double, c_double, c_int, c_int, c_double, i64, u64,
+                                            ctypes.POINTER(u64)]),
+            "mctrg_server_poll": (c_int, [vp, u64, ctypes.POINTER(Estimate), ctypes.POINTER(c_double)]),
+            "mctrg_server_wait": (c_int, [vp, u64, c_double, ctypes.POINTER(Estimate),
+                                          ctypes.POINTER(c_double)]),
+            "mctrg_server_destroy": (None, [vp]),
+            "mctrg_plan_level": (c_int, [c_int, c_int, vp, vp]),
+            "mctrg_philox_uniform": (c_double, [u64, u32, u32, u32, u32]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("output tensors must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("output arrays must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError("expected a numpy array or torch tensor")
+
+
+class MctrgError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (what, mctrg_strerror(status), status))
+
+
+def _check(status, what):
+    if status != MCTRG_OK:
+        raise MctrgError(status, what)
+
+
+def mctrg_strerror(status):
+    return lib().mctrg_strerror(int(status)).decode()
+
+
+def mctrg_options_default():
+    o = Options()
+    _check(lib().mctrg_options_default(ctypes.byref(o)), "mctrg_options_default")
+    return o
+
+
+def make_options(device=0, stream=None, precision=MCTRG_FP64, hbm_budget_bytes=0, max_sweeps=0,
+                 max_chunk=0):
+    o = mctrg_options_default()
+    o.device, o.precision = int(device), int(precision)
+    o.cuda_stream = stream
+    o.hbm_budget_bytes, o.max_sweeps, o.max_chunk = int(hbm_budget_bytes), int(max_sweeps), int(max_chunk)
+    return o
+
+
+def mctrg_create(opts=None):
+    opts = opts or mctrg_options_default()
+    h = ctypes.c_void_p()
+    _check(lib().mctrg_create(ctypes.byref(opts), ctypes.byref(h)), "mctrg_create")
+    return h
+
+
+def mctrg_init_lattice(ctx, beta, h, L, chi):
+    return lib().mctrg_init_lattice(ctx, float(beta), float(h), int(L), int(chi))
+
+
+def mctrg_init_tensor(ctx, T0, D, L, chi):
+    import numpy as np
+    T0 = np.ascontiguousarray(T0, dtype=np.float64)
+    if T0.size != D ** 4:
+        raise ValueError("T0 must hold D^4 values")
+    return lib().mctrg_init_tensor(ctx, T0.ctypes.data, int(D), int(L), int(chi))
+
+
+def mctrg_run(ctx, n_samples, seed, first_traj=0, lnabsZ=None, sign=None, flags=None):
+    """Returns (status, Estimate)."""
+    est = Estimate()
+    s = lib().mctrg_run(ctx, int(n_samples), int(seed), int(first_traj), _ptr(lnabsZ), _ptr(sign),
+                        _ptr(flags), ctypes.byref(est))
+    return s, est
+
+
+def mctrg_footprint(ctx, n_samples):
+    b = ctypes.c_size_t()
+    _check(lib().mctrg_footprint(ctx, int(n_samples), ctypes.byref(b)), "mctrg_footprint")
+    return b.value
+
+
+def mctrg_merge_estimates(parts):
+    arr = (Estimate * len(parts))(*parts)
+    out = Estimate()
+    _check(lib().mctrg_merge_estimates(arr, len(parts), ctypes.byref(out)), "mctrg_merge_estimates")
+    return out
+
+
+def mctrg_destroy(ctx):
+    lib().mctrg_destroy(ctx)
+
+
+def mctrg_plan_level(L, k):
+    """(parity uint8[N_k], parents int64[N_k/2, 4]) of level k, computed by the library."""
+    import numpy as np
+    N = (L * L) >> k
+    par = np.zeros(N, dtype=np.uint8)
+    parents = np.zeros((N // 2, 4), dtype=np.int64)
+    _check(lib().mctrg_plan_level(int(L), int(k), par.ctypes.data, parents.ctypes.data), "mctrg_plan_level")
+    return par, parents
+
+
+def mctrg_philox_uniform(seed, traj, level, tensor, t):
+    return lib().mctrg_philox_uniform(int(seed), int(traj), int(level), int(tensor), int(t))
+
+
+# ---- serving ----
+def mctrg_server_create(opts=None):
+    opts = opts or mctrg_options_default()
+    h = ctypes.c_void_p()
+    _check(lib().mctrg_server_create(ctypes.byref(opts), ctypes.byref(h)), "mctrg_server_create")
+    return h
+
+
+def mctrg_server_submit(srv, beta, h, L, chi, target_se_lnZ, max_samples, seed):
+    jid = ctypes.c_uint64()
+    s = lib().mctrg_server_submit(srv, float(beta), float(h), int(L), int(chi), float(target_se_lnZ),
+                                  int(max_samples), int(seed), ctypes.byref(jid))
+    return s, jid.value
+
+
+def mctrg_server_poll(srv, job_id):
+    est, lat = Estimate(), ctypes.c_double()
+    s = lib().mctrg_server_poll(srv, int(job_id), ctypes.byref(est), ctypes.byref(lat))
+    return s, est, lat.value
+
+
+def mctrg_server_wait(srv, job_id, timeout_s):
+    est, lat = Estimate(), ctypes.c_double()
+    s = lib().mctrg_server_wait(srv, int(job_id), float(timeout_s), ctypes.byref(est), ctypes.byref(lat))
+    return s, est, lat.value
+
+
+def mctrg_server_destroy(srv):
+    lib().mctrg_server_destroy(srv)

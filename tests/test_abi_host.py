@@ -1,0 +1,102 @@
+"""CPU checks of the C-ABI library: it loads, exports every declared symbol,
+and its host-side logic (TRG geometry, Philox stream, estimate merging)
+agrees with the oracle.  No device work is issued."""
+import ctypes
+import glob
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import philox
+from oracle.estimator import estimate
+from oracle.network import plan
+from paper_1710_03757_gb300 import build, mctrg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(mctrg_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared()
+    assert {"mctrg_run", "mctrg_init_lattice", "mctrg_create"} <= names
+    lib = ctypes.CDLL(mctrg.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert names == set(mctrg.EXPORTS)
+
+
+def test_strerror():
+    assert mctrg.mctrg_strerror(0) == "ok"
+    assert "invalid" in mctrg.mctrg_strerror(mctrg.MCTRG_EINVAL)
+
+
+@pytest.mark.parametrize("L", [2, 4, 8, 16, 32])
+def test_geometry_matches_oracle(L):
+    levels = plan(L)
+    for k in range(len(levels) - 1):
+        par, parents = mctrg.mctrg_plan_level(L, k)
+        np.testing.assert_array_equal(par, levels[k].parity)
+        np.testing.assert_array_equal(parents, levels[k].children_parents)
+
+
+def test_geometry_rejects_bad_sizes():
+    lib = mctrg.lib()
+    assert lib.mctrg_plan_level(6, 0, None, None) == mctrg.MCTRG_EINVAL
+    assert lib.mctrg_plan_level(4, 4, None, None) == mctrg.MCTRG_EINVAL
+
+
+def test_philox_matches_oracle():
+    for seed in (0, 1, 0x4D435453, 2 ** 64 - 1):
+        for traj, level, tensor in ((0, 0, 0), (123, 5, 77), (2 ** 32 - 1, 19, 65535)):
+            ref = philox.uniforms(seed, traj, level, tensor, 6)
+            got = [mctrg.mctrg_philox_uniform(seed, traj, level, tensor, t) for t in range(6)]
+            assert got == ref
+
+
+def _est_from(sign, lnabs, scale=None):
+    x_scale = np.max(lnabs[sign != 0]) if scale is None else scale
+    x = np.where(sign != 0, sign * np.exp(np.where(sign != 0, lnabs, x_scale) - x_scale), 0.0)
+    e = mctrg.Estimate()
+    e.n = len(x)
+    e.ln_scale = x_scale
+    e.sum_x = x.sum()
+    e.m2_x = np.sum((x - x.mean()) ** 2)
+    e.n_negative = int(np.sum(sign < 0))
+    return e
+
+
+def test_merge_matches_oracle_on_whole_sample():
+    rng = np.random.default_rng(4)
+    lnabs = 500.0 + rng.normal(0, 2, 3000)
+    sign = np.where(rng.random(3000) < 0.05, -1, 1).astype(np.int8)
+    parts = [_est_from(sign[a:b], lnabs[a:b]) for a, b in ((0, 1000), (1000, 1700), (1700, 3000))]
+    out = mctrg.mctrg_merge_estimates(parts)
+    ref = estimate(sign, lnabs)
+    assert out.n == 3000
+    assert out.ln_scale == ref['ln_scale']
+    assert out.mean_Z_scaled == pytest.approx(ref['mean_Z_scaled'], rel=1e-12)
+    assert out.se_Z_scaled == pytest.approx(ref['se_Z_scaled'], rel=1e-10)
+    assert out.ln_mean_Z == pytest.approx(ref['ln_mean_Z'], rel=1e-14)
+    assert out.ess == pytest.approx(ref['ess'], rel=1e-10)
+    assert out.n_negative == ref['n_negative']
+
+
+def test_merge_rejects_empty():
+    with pytest.raises(mctrg.MctrgError):
+        mctrg.mctrg_merge_estimates([mctrg.Estimate()])

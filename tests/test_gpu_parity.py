@@ -1,0 +1,173 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle.
+
+Per trajectory, on trajectories neither side flags as a near-tie, the sign
+must agree and |ln|Z~|_gpu - ln|Z~|_oracle| <= 1e-10 * max(1, |ln Z|)  (FP64
+everywhere; both sides consume the same Philox stream).  Estimates must lie
+within 3 standard errors of the exact Z where one is known.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ising
+from oracle.estimator import estimate
+from oracle.trg import Problem, run_many
+from paper_1710_03757_gb300 import build, mctrg
+from paper_1710_03757_gb300.workloads import generic_tensor, seed_for
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+    mctrg.lib()
+
+
+def gpu_run(L, chi, n, seed, beta=None, h=0.0, T0=None, first=0, **opts):
+    ctx = mctrg.mctrg_create(mctrg.make_options(**opts))
+    try:
+        if T0 is None:
+            s = mctrg.mctrg_init_lattice(ctx, beta, h, L, chi)
+        else:
+            s = mctrg.mctrg_init_tensor(ctx, T0, T0.shape[0], L, chi)
+        assert s == 0, mctrg.mctrg_strerror(s)
+        lnabs = np.zeros(n)
+        sign = np.zeros(n, dtype=np.int8)
+        flags = np.zeros(n, dtype=np.uint8)
+        st, est = mctrg.mctrg_run(ctx, n, seed, first, lnabs, sign, flags)
+        assert st in (mctrg.MCTRG_OK, mctrg.MCTRG_EDOMAIN), mctrg.mctrg_strerror(st)
+        return est, lnabs, sign, flags
+    finally:
+        mctrg.mctrg_destroy(ctx)
+
+
+def compare(gpu, orc, min_ok=0.5):
+    _, gl, gs, gf = gpu
+    os_, ol, of = orc
+    ok = (gf == 0) & (of == 0)
+    assert ok.mean() >= min_ok, "too many flagged trajectories: %d of %d" % (np.sum(~ok), len(ok))
+    np.testing.assert_array_equal(gs[ok], os_[ok])
+    nz = ok & (os_ != 0)
+    err = np.abs(gl[nz] - ol[nz]) / np.maximum(1.0, np.abs(ol[nz]))
+    assert err.max() <= TOL, "max rel err %.3e at %d" % (err.max(), np.argmax(err))
+    return int(ok.sum())
+
+
+def test_config1_parity_and_unbiased():
+    # 2D Ising 4x4 periodic, h = 0, beta = 0.44, chi = 2, 1000 trajectories
+    seed = seed_for(1)
+    gpu = gpu_run(4, 2, 1000, seed, beta=0.44)
+    orc = run_many(Problem(ising.site_tensor(0.44, 0.0), 4, 2), seed, 0, 1000)
+    compare(gpu, orc, min_ok=0.9)
+    est = gpu[0]
+    z = math.exp(ising.brute_force_lnZ(4, 0.44) - est.ln_scale)
+    assert abs(est.mean_Z_scaled - z) <= 3 * est.se_Z_scaled
+    ref = estimate(orc[0], orc[1])
+    assert est.n_negative == ref['n_negative'] or abs(est.n_negative - ref['n_negative']) <= 5
+
+
+@pytest.mark.parametrize("L,chi,D,n", [(4, 2, 2, 300), (4, 3, 2, 300), (8, 4, 2, 120), (4, 4, 3, 80),
+                                       (2, 2, 2, 300), (8, 3, 3, 40)])
+def test_generic_tensor_parity(L, chi, D, n):
+    T0 = generic_tensor(D, seed=100 + 10 * L + chi + D)
+    seed = 0xC0FFEE + L + chi
+    gpu = gpu_run(L, chi, n, seed, T0=T0)
+    orc = run_many(Problem(T0, L, chi), seed, 0, n)
+    assert compare(gpu, orc, min_ok=0.9) >= 0.9 * n
+
+
+@pytest.mark.parametrize("beta,h,L,chi,n", [(0.3, 0.1, 8, 4, 100), (0.6, 0.0, 4, 2, 300),
+                                             (0.44, 0.05, 8, 2, 200)])
+def test_ising_parity(beta, h, L, chi, n):
+    seed = 991 + L
+    gpu = gpu_run(L, chi, n, seed, beta=beta, h=h)
+    orc = run_many(Problem(ising.site_tensor(beta, h), L, chi), seed, 0, n)
+    compare(gpu, orc, min_ok=0.5)
+
+
+def test_shared_memory_jacobi_n64():
+    # chi = 8: 64 x 64 matrices, Jacobi rows held in shared memory
+    T0 = generic_tensor(2, seed=7)
+    gpu = gpu_run(8, 8, 24, 5, T0=T0)
+    orc = run_many(Problem(T0, 8, 8), 5, 0, 24, workers=4)
+    compare(gpu, orc, min_ok=0.8)
+    gpu = gpu_run(8, 8, 24, 6, beta=0.44)
+    orc = run_many(Problem(ising.site_tensor(0.44, 0.0), 8, 8), 6, 0, 24, workers=4)
+    compare(gpu, orc, min_ok=0.5)
+
+
+def test_global_workspace_jacobi_n256():
+    # chi = 16: 256 x 256 matrices, Jacobi rows in the L2-resident workspace
+    T0 = generic_tensor(2, seed=8)
+    gpu = gpu_run(8, 16, 8, 12, T0=T0)
+    orc = run_many(Problem(T0, 8, 16), 12, 0, 8, workers=4)
+    compare(gpu, orc, min_ok=0.7)
+
+
+def test_exact_path_L2():
+    # chi = 4 >= every rank: no sampling, every trajectory equals Z
+    for beta, h in ((0.44, 0.0), (0.3, 0.2)):
+        est, lnabs, sign, flags = gpu_run(2, 4, 16, 3, beta=beta, h=h)
+        exact = ising.brute_force_lnZ(2, beta, h)
+        assert np.all(sign == 1) and np.all(flags == 0)
+        np.testing.assert_allclose(lnabs, exact, rtol=1e-13)
+        assert est.ln_mean_Z == pytest.approx(exact, rel=1e-13)
+
+
+def test_unbiased_L8_against_kaufman():
+    est, lnabs, sign, flags = gpu_run(8, 4, 20000, seed_for(2), beta=0.4)
+    z = math.exp(ising.kaufman_lnZ(8, 0.4) - est.ln_scale)
+    assert abs(est.mean_Z_scaled - z) <= 3 * est.se_Z_scaled
+
+
+def test_unbiased_field_L4():
+    est, _, _, _ = gpu_run(4, 2, 20000, 4242, beta=0.5, h=0.1)
+    z = math.exp(ising.brute_force_lnZ(4, 0.5, 0.1) - est.ln_scale)
+    assert abs(est.mean_Z_scaled - z) <= 3 * est.se_Z_scaled
+
+
+def test_chunking_and_counter_offsets_do_not_change_trajectories():
+    T0 = generic_tensor(2, seed=21)
+    a = gpu_run(8, 4, 200, 77, T0=T0)
+    b = gpu_run(8, 4, 200, 77, T0=T0, max_chunk=7)
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[2], b[2])
+    c = gpu_run(8, 4, 80, 77, T0=T0, first=120)
+    np.testing.assert_array_equal(a[1][120:], c[1])
+    d = gpu_run(8, 4, 200, 78, T0=T0)
+    assert not np.array_equal(a[1], d[1])
+
+
+def test_device_pointer_outputs():
+    torch = pytest.importorskip("torch")
+    ctx = mctrg.mctrg_create(mctrg.make_options(stream=torch.cuda.current_stream().cuda_stream))
+    try:
+        assert mctrg.mctrg_init_lattice(ctx, 0.44, 0.0, 8, 4) == 0
+        ln = torch.zeros(64, dtype=torch.float64, device="cuda")
+        sg = torch.zeros(64, dtype=torch.int8, device="cuda")
+        fl = torch.zeros(64, dtype=torch.uint8, device="cuda")
+        st, est = mctrg.mctrg_run(ctx, 64, 5, 0, ln, sg, fl)
+        assert st == 0
+        host = np.zeros(64)
+        st2, _ = mctrg.mctrg_run(ctx, 64, 5, 0, host, None, None)
+        np.testing.assert_array_equal(ln.cpu().numpy(), host)
+    finally:
+        mctrg.mctrg_destroy(ctx)
+
+
+def test_error_codes():
+    ctx = mctrg.mctrg_create()
+    try:
+        assert mctrg.mctrg_run(ctx, 10, 1)[0] == mctrg.MCTRG_ESTATE
+        assert mctrg.mctrg_init_lattice(ctx, 0.4, 0.0, 6, 4) == mctrg.MCTRG_EINVAL
+        assert mctrg.mctrg_init_lattice(ctx, 0.4, 0.0, 8, 0) == mctrg.MCTRG_EINVAL
+        assert mctrg.mctrg_init_lattice(ctx, -1.0, 0.0, 8, 4) == mctrg.MCTRG_EINVAL
+        assert mctrg.mctrg_init_lattice(ctx, 0.4, 0.0, 8, 4) == 0
+        assert mctrg.mctrg_run(ctx, 0, 1)[0] == mctrg.MCTRG_EINVAL
+        assert mctrg.mctrg_run(ctx, 10, 1, 2 ** 32 - 5)[0] == mctrg.MCTRG_EINVAL
+        assert mctrg.mctrg_footprint(ctx, 1000) > 0
+    finally:
+        mctrg.mctrg_destroy(ctx)
