@@ -1,0 +1,302 @@
+#!/usr/bin/env python3
+"""Benchmark: Monte Carlo TRG trajectories per second on GB300.
+
+One step = one call of the whole hot path (mctrg_run: sampling, split,
+plaquette contraction, batched Jacobi SVD at every level, final trace,
+estimator) over a batch of trajectories of the workload.  Prints one JSON
+line (rank 0).  `--impl reference` times the CPU oracle on the same
+workload instead.  Under torchrun every rank runs its own trajectory range
+(replicas: no collective on the data path) and rank 0 reports the
+whole-job rate over the slowest rank's time.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# workload name -> (description, parameters)
+WORKLOADS = {
+    # the metric's configuration: 2D Ising 1024 x 1024, chi = 16, plain FP64
+    "ising-L1024-chi16-fp64": dict(L=1024, chi=16, beta=0.44, h=0.0, traj_per_step=1, precision=0),
+    "ising-L256-chi16-fp64": dict(L=256, chi=16, beta=0.44, h=0.0, traj_per_step=8, precision=0),
+    "ising-L32-chi16-fp64": dict(L=32, chi=16, beta=0.44, h=0.0, traj_per_step=512, precision=0),
+    "ising-L16-chi8-fp64": dict(L=16, chi=8, beta=0.44, h=0.0, traj_per_step=4096, precision=0),
+    "ising-L4-chi2-fp64": dict(L=4, chi=2, beta=0.44, h=0.0, traj_per_step=1 << 20, precision=0),
+}
+DEFAULT_WORKLOAD = "ising-L1024-chi16-fp64"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP64 peak of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz = 1.26
+# TFLOP/s (nominal 1.25); a DFMA throughput probe on this machine measured 1.01.
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(wl, seconds_budget=20.0, workers=None):
+    """Oracle (CPU, FP64) trajectories/s for the workload, from a bounded sample.
+
+    Runs whole oracle trajectories on a lattice small enough to finish in the
+    budget with the same chi and level shapes, then scales by the number of
+    per-trajectory tensors at the sampled levels (both grow as L^2), which
+    holds the oracle's work.  Returns (rate, cores, sample description).
+    """
+    import multiprocessing as mp
+    from oracle import ising
+    from oracle.trg import Problem, run_trajectory
+    workers = workers or os.cpu_count() or 1
+    L, chi = wl["L"], wl["chi"]
+    Ls = min(L, 32 if chi >= 16 else (64 if chi >= 8 else 256))
+    prob = Problem(ising.site_tensor(wl["beta"], wl["h"]), Ls, chi)
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    done = 0
+    with ctx.Pool(workers) as pool:
+        batch = workers
+        while True:
+            pool.starmap(run_trajectory, [(prob, 12345, done + i) for i in range(batch)])
+            done += batch
+            if time.perf_counter() - t0 > seconds_budget / 2 or done >= 100000:
+                break
+            batch *= 2
+    dt = time.perf_counter() - t0
+    scale = (L * L) / float(Ls * Ls)
+    rate = done / dt / scale
+    desc = ("oracle, %d whole trajectories of the %dx%d lattice (chi=%d, beta=%g) on %d spawn workers "
+            "in %.1f s, scaled by the per-trajectory tensor count ratio %.0f" % (done, Ls, Ls, chi, wl["beta"],
+                                                                               workers, dt, scale))
+    return rate, workers, desc
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        pass   # the oracle has no device state to warm; each step below is a fresh sample
+    rates = []
+    t_all = time.perf_counter()
+    budget = max(5.0, min(20.0, 150.0 / max(1, args.steps)))
+    for _ in range(args.steps):
+        r, cores, desc = oracle_rate(wl, seconds_budget=budget)
+        rates.append(r)
+    value = sum(rates) / len(rates)
+    line = {"impl": "reference", "metric": "trajectories/s", "value": value, "unit": "trajectories/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * (time.perf_counter() - t_all) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, **{k: wl[k] for k in ("L", "chi", "beta", "h")}},
+            "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--traj-per-step", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = dict(WORKLOADS[args.workload])
+    if args.traj_per_step:
+        wl["traj_per_step"] = args.traj_per_step
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    from paper_1710_03757_gb300 import build, mctrg
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.Stream()
+    opts = mctrg.make_options(device=local, stream=stream.cuda_stream, precision=wl["precision"], profile=1)
+    ctx = mctrg.mctrg_create(opts)
+    s = mctrg.mctrg_init_lattice(ctx, wl["beta"], wl["h"], wl["L"], wl["chi"])
+    if s != 0:
+        raise RuntimeError("init failed: " + mctrg.mctrg_strerror(s))
+    B = wl["traj_per_step"]
+    seed = 0x4D435452 + 2
+    ln_d = torch.zeros(B, dtype=torch.float64, device="cuda")
+    sg_d = torch.zeros(B, dtype=torch.int8, device="cuda")
+    fl_d = torch.zeros(B, dtype=torch.uint8, device="cuda")
+    # trajectory counters: rank r, step s covers [ (s * world + r) * B, ... )
+    step_idx = [0]
+
+    def one_step(host=False):
+        first = (step_idx[0] * world + rank) * B
+        step_idx[0] += 1
+        if host:
+            ln, sg, fl = np.zeros(B), np.zeros(B, np.int8), np.zeros(B, np.uint8)
+        else:
+            ln, sg, fl = ln_d, sg_d, fl_d
+        st, est = mctrg.mctrg_run(ctx, B, seed, first, ln, sg, fl)
+        if st not in (0, mctrg.MCTRG_EDOMAIN, mctrg.MCTRG_ENOCONV):
+            raise RuntimeError("run failed: " + mctrg.mctrg_strerror(st))
+        return est
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    mctrg.mctrg_reset_kernel_stats(ctx)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ests = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ests.append(one_step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    stats = [mctrg.mctrg_kernel_stats(ctx, k) for k in range(mctrg.K_COUNT)]
+    launches = int(sum(st_.launches for st_ in stats))
+    # e2e: the public API call a user makes, host result buffers, wall clock
+    t0 = time.perf_counter()
+    for _ in range(max(1, min(args.steps, 2))):
+        one_step(host=True)
+    e2e_s = (time.perf_counter() - t0) / max(1, min(args.steps, 2))
+    ms_t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max, e2e_max = float(ms_t[0]), float(ms_t[1])
+    total_traj = B * args.steps * world
+    value = total_traj / (ms_max / 1000.0)
+    merged = mctrg.mctrg_merge_estimates(ests)
+    if rank != 0:
+        mctrg.mctrg_destroy(ctx)
+        if dist:
+            dist.destroy_process_group()
+        return
+    # roofline of the dominant kernel (largest summed time)
+    dom = max(range(mctrg.K_COUNT), key=lambda k: stats[k].ms)
+    ds = stats[dom]
+    peaks, peak_src = measured_peaks()
+    if dom in (mctrg.K_JACOBI, mctrg.K_SAMPLE, mctrg.K_FORM_XY, mctrg.K_GEMM, mctrg.K_TRACE) and wl["precision"] == 0:
+        achieved = ds.flops_alg / (ds.ms / 1000.0) / 1e12 if ds.ms > 0 else 0.0
+        peak = FP64_NOMINAL_TFLOPS
+        roof = {"bound": "alu", "kernel": mctrg.KERNEL_NAMES[dom], "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "nominal FP64 (DFMA) rate of GB300; the pool's DFMA probe measured 1.01 TFLOP/s",
+                "traffic": None, "launches": ds.launches, "avg_launch_ms": ds.ms / max(1, ds.launches),
+                "alg_flops_per_launch": ds.flops_alg / max(1, ds.launches)}
+    else:
+        achieved = ds.bytes_alg / (ds.ms / 1000.0) / 1e9 if ds.ms > 0 else 0.0
+        roof = {"bound": "hbm", "kernel": mctrg.KERNEL_NAMES[dom], "achieved": achieved,
+                "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": achieved / peaks.get("hbm_gbs"),
+                "peak_source": peak_src, "traffic": None}
+    kernels = {mctrg.KERNEL_NAMES[k]: {"launches": stats[k].launches, "ms": round(stats[k].ms, 3),
+                                        "share": round(stats[k].ms / max(1e-9, sum(x.ms for x in stats)), 4)}
+               for k in range(mctrg.K_COUNT)}
+    line = {"metric": "trajectories/s", "value": value, "unit": "trajectories/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": ["f64", "f64+tf32", "f64+bf16"][wl["precision"]], "data": "synthetic",
+            "config": {"workload": args.workload, "L": wl["L"], "chi": wl["chi"], "beta": wl["beta"],
+                       "h": wl["h"], "trajectories_per_step_per_gpu": B, "parallelism": "replicas%d" % world,
+                       "l2": "working set (halves, matrices) far larger than L2; no flush needed"},
+            "e2e": {"value": total_traj / args.steps / e2e_max if e2e_max > 0 else None,
+                    "unit": "trajectories/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": B * (8 + 1 + 1) + 8 * 6,
+                    "note": "mctrg_run with host result buffers; inputs are five scalars passed by value"},
+            "gpu_launches": launches, "roofline": roof, "kernels": kernels,
+            "estimate": {"ln_mean_Z": merged.ln_mean_Z, "se_ln_Z": merged.se_ln_Z, "n": merged.n,
+                         "ess": merged.ess, "n_flagged": merged.n_flagged},
+            "clocks": clk.summary()}
+    mctrg.mctrg_destroy(ctx)
+    if not args.no_cpu_baseline:
+        try:
+            r, cores, desc = oracle_rate(wl)
+            line["cpu_baseline"] = {"value": r, "unit": "trajectories/s", "cores": cores, "kind": "oracle",
+                                    "sample": desc}
+        except Exception as e:   # never lose the GPU line over the baseline
+            line["cpu_baseline"] = {"value": None, "error": repr(e)[:200]}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

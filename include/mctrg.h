@@ -71,6 +71,8 @@ typedef struct {
     size_t hbm_budget_bytes;  /* device memory the context may hold; 0 = 80% of free   */
     int max_sweeps;           /* Jacobi sweep cap; 0 = 40                              */
     int max_chunk;            /* max trajectories per device chunk; 0 = automatic      */
+    int profile;              /* 1: time every kernel launch with CUDA events on the
+                                 context's stream (see mctrg_kernel_stats)             */
 } mctrg_options;
 
 /* Estimate of Z from n trajectories (Sec. III Eq. infiniteEnsemble, Sec. V Eq.
@@ -137,6 +139,34 @@ int mctrg_footprint(mctrg_ctx_t ctx, int64_t n_samples, size_t* bytes);
  * seed into *out by rescaling their sufficient statistics to a common scale
  * (host only; the replicas-only multi-GPU merge). */
 int mctrg_merge_estimates(const mctrg_estimate* parts, int k, mctrg_estimate* out);
+
+/* ---- per-kernel statistics (profiling option) -------------------------- *
+ * With mctrg_options.profile = 1, every launch of the hot-path kernels is
+ * bracketed by CUDA events on the context's stream and accumulated per
+ * kernel class since the last reset.  flops_alg is the algorithmic work of
+ * the launches (not the instructions executed):
+ *   JACOBI   (8/3) n^3 + 4 n^2 kc per matrix (SVD floor: bidiagonal reduction
+ *            for all singular values plus the kept singular vectors)
+ *   GEMM     2 n^2 d^2 per tensor (n = D^2 rows/cols, d^2 inner)
+ *   FORM_XY  4 D^2 d^3 per tensor
+ *   SAMPLE   4 n kc + 2 n^2 kc per tensor (tables and draws; left halves M v)
+ *   TRACE    2 D^2 d^2 per trajectory
+ * bytes_alg counts each kernel's compulsory global-memory traffic
+ * (inputs read once, outputs written once). */
+enum { MCTRG_K_FORM_XY = 0, MCTRG_K_GEMM = 1, MCTRG_K_JACOBI = 2, MCTRG_K_SAMPLE = 3,
+       MCTRG_K_TRACE = 4, MCTRG_K_OTHER = 5, MCTRG_K_COUNT = 6 };
+typedef struct {
+    int64_t launches;
+    double ms;          /* summed event-timed duration */
+    int64_t items;      /* matrices / tensors / trajectories processed */
+    double flops_alg;
+    double bytes_alg;
+} mctrg_kernel_stat;
+
+/* Statistics of kernel class `kernel` (MCTRG_K_*) since the last reset.
+ * Errors: EINVAL (bad class), ESTATE (profiling off). */
+int mctrg_kernel_stats(mctrg_ctx_t ctx, int kernel, mctrg_kernel_stat* out);
+int mctrg_reset_kernel_stats(mctrg_ctx_t ctx);
 
 /* Release every resource of the context (NULL is a no-op). */
 void mctrg_destroy(mctrg_ctx_t ctx);

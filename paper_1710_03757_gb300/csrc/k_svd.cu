@@ -172,7 +172,275 @@ __global__ void k_jacobi(JacobiArgs a, int use_smem, int G) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-batched variant for n > 32 (one lane group = the whole warp).
+//
+// Each warp takes PW disjoint pairs of a round-robin step.  Their PW dot
+// products are reduced together by recursive halving (lane bit 4 picks the
+// upper or lower half of the pair set, then bit 3, ...), which costs about
+// PW additions per lane instead of 5 PW, and leaves the total of pair
+// j = lane >> (5 - log2 PW) in every lane; each lane then computes the
+// rotation of "its" pair, so the divisions and square roots are shared by
+// the PW pairs.  Rotations use scaled rows (Anda and Park 1994, fast plane
+// rotations): the true row is d_r * row_r; the rotation by tangent t,
+// cosine c becomes
+//   row_p <- row_p - t (d_q / d_p) row_q,  row_q <- row_q + t (d_p / d_q) row_p,
+//   d_p <- c d_p,  d_q <- c d_q,
+// two FMAs per element instead of four.  With |t| <= 1 each rotation scales
+// d by at least 2^-1/2, and the scales are folded back into the rows at every
+// sweep start, so d stays above 2^-(n-1)/2.  True squared norms are carried
+// separately and recomputed exactly at every sweep start.
+template <int PW>
+__device__ __forceinline__ double batched_reduce(double (&v)[PW], int lane) {
+  int cnt = PW;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    if (cnt > 1) {
+      const int half = cnt >> 1;
+      const bool upper = (lane & o) != 0;
+#pragma unroll
+      for (int k = 0; k < PW / 2; ++k) {
+        if (k < half) {
+          const double send = upper ? v[k] : v[k + half];
+          const double keep = upper ? v[k + half] : v[k];
+          v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+      cnt = half;
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    }
+  }
+  return v[0];
+}
+
+template <int PW>
+__global__ void __launch_bounds__(512) k_jacobi_warp(JacobiArgs a, int use_smem) {
+  extern __shared__ double smem[];
+  __shared__ int s_rot, s_na;
+  __shared__ double s_thr2;
+  constexpr int LOGPW = PW == 1 ? 0 : PW == 2 ? 1 : PW == 4 ? 2 : PW == 8 ? 3 : PW == 16 ? 4 : 5;
+  constexpr int SH = 5 - LOGPW;                    // lane >> SH = pair index within the warp
+  const int mat = blockIdx.x;
+  const int n = a.n, np = a.n_pad;
+  double* A = use_smem ? smem : a.W + (size_t)mat * np * n;
+  double* nrm = use_smem ? smem + (size_t)np * n : smem;
+  double* dsc = nrm + np;                          // [np] row scales
+  int* act = (int*)(dsc + np);                     // [np + 1] active rows
+  const double* Mm = a.M + (size_t)mat * n * n;
+  for (int idx = threadIdx.x; idx < np * n; idx += blockDim.x) A[idx] = idx < n * n ? Mm[idx] : 0.0;
+  for (int r = threadIdx.x; r < np; r += blockDim.x) dsc[r] = 1.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const double tol = (double)np * 0x1.0p-53;
+  bool converged = false;
+
+  for (int sweep = 0; sweep < a.max_sweeps && !converged; ++sweep) {
+    // fold the scales into the rows and take exact squared norms
+    for (int r = warp; r < np; r += nwarps) {
+      const double dr = dsc[r];
+      double s = 0.0;
+      double* row = A + (size_t)r * n;
+      for (int c = lane; c < n; c += 32) {
+        double v = row[c];
+        if (dr != 1.0) { v *= dr; row[c] = v; }
+        s = fma(v, v, s);
+      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) { nrm[r] = s; dsc[r] = 1.0; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (sweep == 0) {
+        double f = 0.0;
+        for (int r = 0; r < np; ++r) f += nrm[r];
+        s_thr2 = f * 0x1.0p-106;
+      }
+      int na = 0;
+      for (int r = 0; r < np; ++r)
+        if (nrm[r] > s_thr2) act[na++] = r;
+      if (na & 1) act[na] = -1;
+      s_na = na;
+      s_rot = 0;
+    }
+    __syncthreads();
+    const int na = s_na, nap = na + (na & 1), npairs = nap >> 1;
+    for (int step = 0; step + 1 < nap; ++step) {
+      int myrot = 0;
+      for (int base = warp * PW; base < npairs; base += nwarps * PW) {
+        int Pj[PW], Qj[PW];
+        double g[PW];
+#pragma unroll
+        for (int j = 0; j < PW; ++j) {
+          const int pk = base + j;
+          int P = -1, Q = -1;
+          if (pk < npairs) {
+            P = act[pk == 0 ? 0 : 1 + (pk - 1 + step) % (nap - 1)];
+            Q = act[1 + (nap - 2 - pk + step) % (nap - 1)];
+          }
+          Pj[j] = P; Qj[j] = Q;
+          double acc = 0.0;
+          if (P >= 0 && Q >= 0) {
+            const double* ap = A + (size_t)P * n;
+            const double* aq = A + (size_t)Q * n;
+            for (int c = lane; c < n; c += 32) acc = fma(ap[c], aq[c], acc);
+          }
+          g[j] = acc;
+        }
+        const double gs = batched_reduce<PW>(g, lane);
+        // this lane's pair
+        const int jm = lane >> SH;
+        int P = -1, Q = -1;
+#pragma unroll
+        for (int j = 0; j < PW; ++j) if (j == jm) { P = Pj[j]; Q = Qj[j]; }
+        bool rot = false;
+        double mu1 = 0.0, mu2 = 0.0, cs = 1.0, nal = 0.0, nbe = 0.0, al = 0.0, be = 0.0;
+        if (P >= 0 && Q >= 0) {
+          al = nrm[P]; be = nrm[Q];
+          const double dp = dsc[P], dq = dsc[Q];
+          const double gam = dp * dq * gs;
+          rot = al > 0.0 && be > 0.0 && fabs(gam) > tol * sqrt(al) * sqrt(be);
+          if (rot) {
+            const double zeta = (be - al) / (2.0 * gam);
+            double t;
+            if (fabs(zeta) > 1e150) t = 0.5 / zeta;
+            else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+            cs = 1.0 / sqrt(fma(t, t, 1.0));
+            mu1 = t * (dq / dp);
+            mu2 = t * (dp / dq);
+            nal = fma(-t, gam, al);
+            nbe = fma(t, gam, be);
+          }
+        }
+        bool fixany = false;
+#pragma unroll
+        for (int j = 0; j < PW; ++j) {
+          const int src = j << SH;
+          const bool rj = __shfl_sync(0xffffffffu, rot, src);
+          if (!rj) continue;                                   // warp-uniform
+          const double m1 = __shfl_sync(0xffffffffu, mu1, src);
+          const double m2 = __shfl_sync(0xffffffffu, mu2, src);
+          double* ap = A + (size_t)Pj[j] * n;
+          double* aq = A + (size_t)Qj[j] * n;
+          for (int c = lane; c < n; c += 32) {
+            const double x = ap[c], y = aq[c];
+            ap[c] = fma(-m1, y, x);
+            aq[c] = fma(m2, x, y);
+          }
+        }
+        const bool own = (lane & ((1 << SH) - 1)) == 0;
+        const bool fixP = rot && nal < 0.01 * al, fixQ = rot && nbe < 0.01 * be;
+        if (own && rot) {
+          nrm[P] = nal; nrm[Q] = nbe;
+          dsc[P] *= cs; dsc[Q] *= cs;
+          ++myrot;
+        }
+        fixany = __any_sync(0xffffffffu, fixP || fixQ);
+        if (fixany) {                                          // rare: recompute from the rows
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < PW; ++j) {
+            const int src = j << SH;
+            const bool fp = __shfl_sync(0xffffffffu, fixP, src), fq = __shfl_sync(0xffffffffu, fixQ, src);
+            for (int side = 0; side < 2; ++side) {
+              if (!(side == 0 ? fp : fq)) continue;            // warp-uniform
+              const int r = side == 0 ? Pj[j] : Qj[j];
+              const double* row = A + (size_t)r * n;
+              const double dr = dsc[r];
+              double s = 0.0;
+              for (int c = lane; c < n; c += 32) s = fma(row[c], row[c], s);
+              for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+              if (lane == 0) nrm[r] = s * dr * dr;
+            }
+          }
+          __syncwarp();
+        }
+      }
+      if (myrot) atomicAdd(&s_rot, myrot);
+      __syncthreads();
+    }
+    converged = (s_rot == 0);
+    __syncthreads();
+  }
+  // true rows and exact norms
+  for (int r = warp; r < np; r += nwarps) {
+    const double dr = dsc[r];
+    double s = 0.0;
+    double* row = A + (size_t)r * n;
+    for (int c = lane; c < n; c += 32) {
+      double v = row[c];
+      if (dr != 1.0) { v *= dr; row[c] = v; }
+      s = fma(v, v, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) nrm[r] = sqrt(s);
+  }
+  __syncthreads();
+  double* sg = a.sig + (size_t)mat * np;
+  int* pm = a.perm + (size_t)mat * np;
+  for (int r = threadIdx.x; r < np; r += blockDim.x) {
+    const double v = nrm[r];
+    int rank = 0;
+    for (int j = 0; j < np; ++j) {
+      const double u = nrm[j];
+      rank += (u > v) || (u == v && j < r);
+    }
+    sg[rank] = v;
+    pm[rank] = r;
+  }
+  if (use_smem) {
+    double* Wm = a.W + (size_t)mat * np * n;
+    for (int idx = threadIdx.x; idx < np * n; idx += blockDim.x) Wm[idx] = A[idx];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double s1 = sg[0];
+    if (a.lns1) a.lns1[mat] = s1 > 0.0 ? log(s1) : -INFINITY;
+    const double tau = (double)n * 0x1.0p-52 * s1;
+    int cnt = 0;
+    for (int r = 0; r < np; ++r) cnt += sg[r] > tau;
+    a.nnz[mat] = s1 > 0.0 ? cnt : 0;
+    if (a.mflags && !converged) a.mflags[mat] |= FLAG_NOCONV;
+  }
+}
+
+template <int PW>
+static cudaError_t launch_warp_variant(const JacobiArgs& a, int threads, cudaStream_t st) {
+  const int n = a.n, np = a.n_pad;
+  const size_t rows_bytes = (size_t)np * n * sizeof(double);
+  const size_t aux = (size_t)np * 2 * sizeof(double) + (size_t)(np + 2) * sizeof(int);
+  const int use_smem = (rows_bytes + aux) <= 200 * 1024;
+  const size_t smem = use_smem ? rows_bytes + aux : std::max<size_t>(aux, 120 * 1024);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_jacobi_warp<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 64);
+    attr = true;
+  }
+  k_jacobi_warp<PW><<<a.S, threads, smem, st>>>(a, use_smem);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_jacobi(const JacobiArgs& a, cudaStream_t st) {
+  if (a.S <= 0) return cudaSuccess;
+  if (a.n > 32) {
+    // pairs per warp so that one pass of the warps covers a step
+    const int npairs = a.n_pad / 2;
+    const int threads = a.n <= 64 ? 256 : 512;
+    const int nw = threads / 32;
+    int pw = 1;
+    while (pw < 32 && pw * nw < npairs) pw <<= 1;
+    switch (pw) {
+      case 1: return launch_warp_variant<1>(a, threads, st);
+      case 2: return launch_warp_variant<2>(a, threads, st);
+      case 4: return launch_warp_variant<4>(a, threads, st);
+      case 8: return launch_warp_variant<8>(a, threads, st);
+      case 16: return launch_warp_variant<16>(a, threads, st);
+      default: return launch_warp_variant<32>(a, threads, st);
+    }
+  }
+
+  // n <= 32: lane groups of G < 32 lanes per pair
+
   if (a.S <= 0) return cudaSuccess;
   const int n = a.n, np = a.n_pad;
   const size_t rows_bytes = (size_t)np * n * sizeof(double);

@@ -121,7 +121,44 @@ extern "C" const char* mctrg_strerror(int s) {
   }
 }
 
+cudaEvent_t mctrg_ctx::take_event() {
+  if (!event_pool.empty()) {
+    cudaEvent_t e = event_pool.back();
+    event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void mctrg_ctx::resolve_events() {
+  for (const Pending& p : pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) kstat[p.cls].ms += ms;
+    event_pool.push_back(p.a);
+    event_pool.push_back(p.b);
+  }
+  pending.clear();
+}
+
+extern "C" int mctrg_kernel_stats(mctrg_ctx_t c, int kernel, mctrg_kernel_stat* out) {
+  if (!c || !out || kernel < 0 || kernel >= MCTRG_K_COUNT) return MCTRG_EINVAL;
+  if (!c->opt.profile) return MCTRG_ESTATE;
+  *out = c->kstat[kernel];
+  return MCTRG_OK;
+}
+
+extern "C" int mctrg_reset_kernel_stats(mctrg_ctx_t c) {
+  if (!c) return MCTRG_EINVAL;
+  for (auto& k : c->kstat) k = mctrg_kernel_stat{};
+  return MCTRG_OK;
+}
+
 void mctrg_ctx::release_all() {
+  resolve_events();
+  for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
+  event_pool.clear();
   DevBuf* all[] = {&T0, &shM, &shW, &shSig, &shPerm, &shNnz, &shLns1, &shU, &shH, &Hbuf[0], &Hbuf[1],
                    &Mb, &Wb, &Xb, &Yb, &sigb, &permb, &nnzb, &ilns1, &iflags, &lnacc, &tflags,
                    &scratch, &o_lnabs, &o_sign, &o_flags, &o_tflags, &stats};
@@ -395,9 +432,11 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
         sa.item0 = 0; sa.n_items = items; sa.N = a.N; sa.L = L; sa.level = s0; sa.seed = seed;
         sa.traj0 = traj0; sa.H = Hbuf[cur].as<double>(); sa.h_item0 = 0; sa.iflags = iflags.as<uint32_t>();
         sa.scratch = scratch.as<double>();
-        CK(launch_sample_split(sa, st, grid_s));
-        CK(launch_traj_accum(nullptr, iflags.as<uint32_t>(), a.N, Bc, lnacc.as<double>(),
-                             o_tflags.as<uint32_t>(), st));
+        CK(timed(MCTRG_K_SAMPLE, items, items * (4.0 * a.n * a.kc),
+                 8.0 * items * (2.0 * a.n * a.kc + a.n_pad), [&] { return launch_sample_split(sa, st, grid_s); }));
+        CK(timed(MCTRG_K_OTHER, Bc, 0.0, 4.0 * items, [&] {
+          return launch_traj_accum(nullptr, iflags.as<uint32_t>(), a.N, Bc, lnacc.as<double>(),
+                                   o_tflags.as<uint32_t>(), st); }));
       }
       for (int k = s0 + 1; k < nlev; ++k) {
         const LevelInfo& a = lv[k];
@@ -412,18 +451,23 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
           xa.H = Hbuf[prev].as<double>(); xa.h_item0 = 0; xa.d = p.D; xa.D = p.kc; xa.c0 = i0;
           xa.n_items = Si; xa.Nnew = a.N; xa.Nold = p.N; xa.L = L; xa.level_old = k - 1;
           xa.fixed_parents = 0; xa.X = Xb.as<double>(); xa.Yt = Yb.as<double>();
-          CK(launch_form_xy(xa, st));
+          const double D2 = (double)p.kc * p.kc, dd = p.D;
+          CK(timed(MCTRG_K_FORM_XY, Si, Si * 4.0 * D2 * dd * dd * dd,
+                   8.0 * Si * (4.0 * p.kc * dd * dd + 2.0 * D2 * dd * dd), [&] { return launch_form_xy(xa, st); }));
           GemmArgs gm{};
           gm.X = Xb.as<double>(); gm.Yt = Yb.as<double>(); gm.M = Mb.as<double>(); gm.D = a.D;
           gm.K = p.D * p.D; gm.c0 = i0; gm.n_items = Si; gm.Nnew = a.N; gm.L = L; gm.level_new = k;
           gm.fixed_parity = -1;
-          CK(launch_gemm_f64(gm, st));
+          CK(timed(MCTRG_K_GEMM, Si, Si * 2.0 * a.n * a.n * gm.K, 8.0 * Si * (2.0 * a.n * gm.K + (double)a.n * a.n),
+                   [&] { return launch_gemm_f64(gm, st); }));
           JacobiArgs ja{};
           ja.M = Mb.as<double>(); ja.W = Wb.as<double>(); ja.sig = sigb.as<double>();
           ja.perm = permb.as<int>(); ja.lns1 = ilns1.as<double>() + i0; ja.nnz = nnzb.as<int>();
           ja.mflags = iflags.as<uint32_t>() + i0; ja.n = a.n; ja.n_pad = a.n_pad; ja.S = (int)Si;
           ja.max_sweeps = opt.max_sweeps;
-          CK(launch_jacobi(ja, st));
+          const double nn = a.n;
+          CK(timed(MCTRG_K_JACOBI, Si, Si * ((8.0 / 3.0) * nn * nn * nn + 4.0 * nn * nn * a.kc),
+                   8.0 * Si * (nn * nn + (double)a.n_pad * nn + 1.5 * a.n_pad), [&] { return launch_jacobi(ja, st); }));
           SampleArgs sa{};
           sa.M = Mb.as<double>(); sa.W = Wb.as<double>(); sa.sig = sigb.as<double>();
           sa.perm = permb.as<int>(); sa.nnz = nnzb.as<int>(); sa.Urows = nullptr;
@@ -431,10 +475,12 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
           sa.item0 = i0; sa.n_items = Si; sa.N = a.N; sa.L = L; sa.level = k; sa.seed = seed;
           sa.traj0 = traj0; sa.H = Hbuf[cur].as<double>(); sa.h_item0 = 0;
           sa.iflags = iflags.as<uint32_t>(); sa.scratch = scratch.as<double>();
-          CK(launch_sample_split(sa, st, grid_s));
+          CK(timed(MCTRG_K_SAMPLE, Si, Si * (4.0 * nn * a.kc + 2.0 * nn * nn * a.kc),
+                   8.0 * Si * (2.0 * nn * nn + 2.0 * nn * a.kc), [&] { return launch_sample_split(sa, st, grid_s); }));
         }
-        CK(launch_traj_accum(ilns1.as<double>(), iflags.as<uint32_t>(), a.N, Bc, lnacc.as<double>(),
-                             o_tflags.as<uint32_t>(), st));
+        CK(timed(MCTRG_K_OTHER, Bc, 0.0, 12.0 * items, [&] {
+          return launch_traj_accum(ilns1.as<double>(), iflags.as<uint32_t>(), a.N, Bc, lnacc.as<double>(),
+                                   o_tflags.as<uint32_t>(), st); }));
       }
       {  // final contraction and trace
         const LevelInfo& p = lv[nlev - 1];
@@ -442,21 +488,27 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
         xa.H = Hbuf[cur].as<double>(); xa.h_item0 = 0; xa.d = p.D; xa.D = p.kc; xa.c0 = 0;
         xa.n_items = Bc; xa.Nnew = 1; xa.Nold = p.N; xa.L = L; xa.level_old = nlev - 1;
         xa.fixed_parents = 0; xa.X = Xb.as<double>(); xa.Yt = Yb.as<double>();
-        CK(launch_form_xy(xa, st));
-        CK(launch_trace(Xb.as<double>(), Yb.as<double>(), (int64_t)p.kc * p.kc * p.n, Bc, lnacc0,
-                        lnacc.as<double>(), o_lnabs.as<double>() + c0, o_sign.as<int8_t>() + c0, st));
-        CK(launch_flags_to_u8(o_tflags.as<uint32_t>(), o_flags.as<uint8_t>() + c0, Bc, st));
+        const double D2 = (double)p.kc * p.kc, dd = p.D;
+        CK(timed(MCTRG_K_FORM_XY, Bc, Bc * 4.0 * D2 * dd * dd * dd,
+                 8.0 * Bc * (4.0 * p.kc * dd * dd + 2.0 * D2 * dd * dd), [&] { return launch_form_xy(xa, st); }));
+        CK(timed(MCTRG_K_TRACE, Bc, Bc * 2.0 * D2 * p.n, 8.0 * Bc * 2.0 * D2 * p.n, [&] {
+          return launch_trace(Xb.as<double>(), Yb.as<double>(), (int64_t)p.kc * p.kc * p.n, Bc, lnacc0,
+                              lnacc.as<double>(), o_lnabs.as<double>() + c0, o_sign.as<int8_t>() + c0, st); }));
+        CK(timed(MCTRG_K_OTHER, Bc, 0.0, 5.0 * Bc, [&] {
+          return launch_flags_to_u8(o_tflags.as<uint32_t>(), o_flags.as<uint8_t>() + c0, Bc, st); }));
       }
     }
   }
-  CK(launch_estimate(o_lnabs.as<double>(), o_sign.as<int8_t>(), o_flags.as<uint8_t>(), n,
-                     stats.as<double>(), st));
+  CK(timed(MCTRG_K_OTHER, n, 0.0, 10.0 * n, [&] {
+    return launch_estimate(o_lnabs.as<double>(), o_sign.as<int8_t>(), o_flags.as<uint8_t>(), n,
+                           stats.as<double>(), st); }));
   double hs[6];
   CK(cudaMemcpyAsync(hs, stats.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
   if (lnabs_out) CK(cudaMemcpyAsync(lnabs_out, o_lnabs.p, sizeof(double) * n, cudaMemcpyDefault, st));
   if (sign_out) CK(cudaMemcpyAsync(sign_out, o_sign.p, (size_t)n, cudaMemcpyDefault, st));
   if (flags_out) CK(cudaMemcpyAsync(flags_out, o_flags.p, (size_t)n, cudaMemcpyDefault, st));
   CK(cudaStreamSynchronize(st));
+  resolve_events();
   finalize_estimate(hs, n, est);
   // any trajectory whose SVD hit the sweep cap
   if (est->status == MCTRG_OK && any_noconv(n)) est->status = MCTRG_ENOCONV;

@@ -48,6 +48,36 @@ struct mctrg_ctx {
   mctrg::DevBuf Hbuf[2], Mb, Wb, Xb, Yb, sigb, permb, nnzb, ilns1, iflags, lnacc, tflags, scratch;
   mctrg::DevBuf o_lnabs, o_sign, o_flags, o_tflags, stats;
 
+  // per-kernel-class statistics (MCTRG_K_*)
+  mctrg_kernel_stat kstat[MCTRG_K_COUNT]{};
+  struct Pending { int cls; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  // Launch through f(); counts it, and with profiling brackets it with events.
+  template <class F>
+  cudaError_t timed(int cls, int64_t items, double flops, double bytes, F&& f) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (opt.profile) {
+      a = take_event();
+      b = take_event();
+      if (!a || !b) return cudaErrorMemoryAllocation;
+      cudaEventRecord(a, st);
+    }
+    cudaError_t e = f();
+    if (e != cudaSuccess) return e;
+    if (opt.profile) {
+      cudaEventRecord(b, st);
+      pending.push_back(Pending{cls, a, b});
+    }
+    kstat[cls].launches += 1;
+    kstat[cls].items += items;
+    kstat[cls].flops_alg += flops;
+    kstat[cls].bytes_alg += bytes;
+    return cudaSuccess;
+  }
+  cudaEvent_t take_event();
+  void resolve_events();   // after a stream synchronize
+
   int init_from_device_tensor(int D0, int L, int chi);
   void plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& total) const;
   int run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs, int8_t* sign, uint8_t* flags,

@@ -21,14 +21,22 @@ EXPORTS = [
     "mctrg_options_default", "mctrg_create", "mctrg_init_lattice", "mctrg_init_tensor",
     "mctrg_run", "mctrg_footprint", "mctrg_merge_estimates", "mctrg_destroy", "mctrg_strerror",
     "mctrg_server_create", "mctrg_server_submit", "mctrg_server_poll", "mctrg_server_wait",
-    "mctrg_server_destroy", "mctrg_plan_level", "mctrg_philox_uniform",
+    "mctrg_server_destroy", "mctrg_plan_level", "mctrg_philox_uniform", "mctrg_kernel_stats",
+    "mctrg_reset_kernel_stats",
 ]
+K_FORM_XY, K_GEMM, K_JACOBI, K_SAMPLE, K_TRACE, K_OTHER, K_COUNT = range(7)
+KERNEL_NAMES = ["form_xy", "gemm", "jacobi", "sample_split", "trace", "other"]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("items", ctypes.c_int64),
+                ("flops_alg", ctypes.c_double), ("bytes_alg", ctypes.c_double)]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("max_sweeps", ctypes.c_int),
-                ("max_chunk", ctypes.c_int)]
+                ("max_chunk", ctypes.c_int), ("profile", ctypes.c_int)]
 
 
 class Estimate(ctypes.Structure):
@@ -74,6 +82,8 @@ def lib():
             "mctrg_server_destroy": (None, [vp]),
             "mctrg_plan_level": (c_int, [c_int, c_int, vp, vp]),
             "mctrg_philox_uniform": (c_double, [u64, u32, u32, u32, u32]),
+            "mctrg_kernel_stats": (c_int, [vp, c_int, ctypes.POINTER(KernelStat)]),
+            "mctrg_reset_kernel_stats": (c_int, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -120,9 +130,9 @@ def mctrg_options_default():
 
 
 def make_options(device=0, stream=None, precision=MCTRG_FP64, hbm_budget_bytes=0, max_sweeps=0,
-                 max_chunk=0):
+                 max_chunk=0, profile=0):
     o = mctrg_options_default()
-    o.device, o.precision = int(device), int(precision)
+    o.device, o.precision, o.profile = int(device), int(precision), int(profile)
     o.cuda_stream = stream
     o.hbm_budget_bytes, o.max_sweeps, o.max_chunk = int(hbm_budget_bytes), int(max_sweeps), int(max_chunk)
     return o
@@ -166,6 +176,16 @@ def mctrg_merge_estimates(parts):
     out = Estimate()
     _check(lib().mctrg_merge_estimates(arr, len(parts), ctypes.byref(out)), "mctrg_merge_estimates")
     return out
+
+
+def mctrg_kernel_stats(ctx, kernel):
+    st = KernelStat()
+    _check(lib().mctrg_kernel_stats(ctx, int(kernel), ctypes.byref(st)), "mctrg_kernel_stats")
+    return st
+
+
+def mctrg_reset_kernel_stats(ctx):
+    _check(lib().mctrg_reset_kernel_stats(ctx), "mctrg_reset_kernel_stats")
 
 
 def mctrg_destroy(ctx):
