@@ -168,6 +168,22 @@ typedef struct {
 int mctrg_kernel_stats(mctrg_ctx_t ctx, int kernel, mctrg_kernel_stat* out);
 int mctrg_reset_kernel_stats(mctrg_ctx_t ctx);
 
+/* ---- the batched SVD on its own ------------------------------------------ *
+ * Singular values, and optionally right singular vectors, of `batch` row-major
+ * n x n FP64 matrices by the library's batched one-sided Jacobi SVD (the full
+ * SVD of Sec. II, Eq. exactSVD, that every tensor of a trajectory goes
+ * through).  M (device, batch*n*n) is read only.  sigma (device, batch*n)
+ * receives the singular values in descending order; vt (device, batch*n*n,
+ * may be NULL) receives the right singular vectors as rows in the same order
+ * (zero rows for singular values that are exactly zero).  1 <= n <= 1024,
+ * batch >= 1, max_sweeps <= 0 means 40.  Allocates its working rows on the
+ * device for the call and frees them; runs on `stream` (cudaStream_t, NULL =
+ * default) and returns once the stream has completed.
+ * Errors: EINVAL, ENOMEM, ECUDA, ENOCONV (a matrix hit the sweep cap; results
+ * still written). */
+int mctrg_svd_batched(const double* M, int n, int64_t batch, double* sigma, double* vt,
+                      int max_sweeps, void* stream);
+
 /* Release every resource of the context (NULL is a no-op). */
 void mctrg_destroy(mctrg_ctx_t ctx);
 
