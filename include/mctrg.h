@@ -184,6 +184,29 @@ int mctrg_reset_kernel_stats(mctrg_ctx_t ctx);
 int mctrg_svd_batched(const double* M, int n, int64_t batch, double* sigma, double* vt,
                       int max_sweeps, void* stream);
 
+/* The same batched SVD for callers that cannot allocate device memory.
+ * There is no counterpart in the paper: it exists for callers such as a
+ * program whose device memory belongs to another allocator (for example a
+ * framework's caching allocator holding nearly all of it), a loop that must
+ * never stall the device (cudaFree, which mctrg_svd_batched calls, waits for
+ * the whole device), or code that may not call an allocator at all.
+ * Arguments and results are those of mctrg_svd_batched; the caller still
+ * provides M, sigma and vt.  The working memory is one fixed 16 MiB array
+ * compiled into the library, which every device that loads the library holds
+ * until the process exits; no allocation or free of any kind happens.
+ * n may be at most MCTRG_SVD_NOALLOC_MAX_N (larger n returns MCTRG_EINVAL);
+ * any batch size works (the batch is processed in pieces that fit).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * reuses the same array and its flag word is cleared at the start of each
+ * call; two calls whose work overlapped on the device would race, so calls
+ * from one process are serialized and each returns only after `stream` has
+ * completed.  `stream` must belong to the current device.
+ * Errors: EINVAL, ECUDA, ENOCONV. */
+#define MCTRG_SVD_NOALLOC_MAX_N 1024
+int mctrg_svd_batched_noalloc(const double* M, int n, int64_t batch, double* sigma, double* vt,
+                              int max_sweeps, void* stream);
+
 /* Release every resource of the context (NULL is a no-op). */
 void mctrg_destroy(mctrg_ctx_t ctx);
 

@@ -22,7 +22,7 @@ EXPORTS = [
     "mctrg_run", "mctrg_footprint", "mctrg_merge_estimates", "mctrg_destroy", "mctrg_strerror",
     "mctrg_server_create", "mctrg_server_submit", "mctrg_server_poll", "mctrg_server_wait",
     "mctrg_server_destroy", "mctrg_plan_level", "mctrg_philox_uniform", "mctrg_kernel_stats",
-    "mctrg_reset_kernel_stats", "mctrg_svd_batched",
+    "mctrg_reset_kernel_stats", "mctrg_svd_batched", "mctrg_svd_batched_noalloc",
 ]
 K_FORM_XY, K_GEMM, K_JACOBI, K_SAMPLE, K_TRACE, K_OTHER, K_COUNT = range(7)
 KERNEL_NAMES = ["form_xy", "gemm", "jacobi", "sample_split", "trace", "other"]
@@ -85,6 +85,7 @@ def lib():
             "mctrg_kernel_stats": (c_int, [vp, c_int, ctypes.POINTER(KernelStat)]),
             "mctrg_reset_kernel_stats": (c_int, [vp]),
             "mctrg_svd_batched": (c_int, [vp, c_int, i64, vp, vp, c_int, vp]),
+            "mctrg_svd_batched_noalloc": (c_int, [vp, c_int, i64, vp, vp, c_int, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -193,6 +194,13 @@ def mctrg_svd_batched(M, sigma, vt=None, max_sweeps=0, stream=None):
     """M: device tensor (batch, n, n) float64; sigma: (batch, n); vt: (batch, n, n) or None."""
     batch, n = int(M.shape[0]), int(M.shape[-1])
     return lib().mctrg_svd_batched(_ptr(M), n, batch, _ptr(sigma), _ptr(vt), int(max_sweeps), stream)
+
+
+def mctrg_svd_batched_noalloc(M, sigma, vt=None, max_sweeps=0, stream=None):
+    """As mctrg_svd_batched, with the library's fixed working array instead of
+    device allocations (for callers that cannot allocate)."""
+    batch, n = int(M.shape[0]), int(M.shape[-1])
+    return lib().mctrg_svd_batched_noalloc(_ptr(M), n, batch, _ptr(sigma), _ptr(vt), int(max_sweeps), stream)
 
 
 def mctrg_destroy(ctx):
