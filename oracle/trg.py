@@ -71,8 +71,15 @@ def split(T, parity, Dn, choose):
 
 
 def contract(F3, F4, F2, F1):
-    """T'[al,be,de,ga] = sum F3[al,i,j] F4[be,k,i] F2[j,m,ga] F1[m,k,de]."""
-    return np.einsum('aij,bki,jmg,mkd->abdg', F3, F4, F2, F1)
+    """T'[al,be,de,ga] = sum F3[al,i,j] F4[be,k,i] F2[j,m,ga] F1[m,k,de].
+
+    Summed pairwise in the Levin-Nave order (Sec. III): X = F3 F4 over i,
+    Y = F2 F1 over m, then X Y over (j, k).  Same sum as the four-tensor
+    expression, in a different rounding order.
+    """
+    X = np.einsum('aij,bki->abjk', F3, F4)
+    Y = np.einsum('jmg,mkd->jkdg', F2, F1)
+    return np.tensordot(X, Y, axes=([2, 3], [0, 1]))
 
 
 class Problem:
@@ -167,10 +174,22 @@ def run_many(prob, seed, first_traj, n, workers=1):
         res = [run_trajectory(prob, seed, i) for i in trajs]
     else:
         import multiprocessing as mp
-        ctx = mp.get_context('spawn')
-        with ctx.Pool(workers) as pool:
-            res = pool.starmap(run_trajectory, [(prob, seed, i) for i in trajs],
-                               chunksize=max(1, n // (4 * workers)))
+        import os
+        # one BLAS thread per worker: the workers are the parallelism
+        saved = {k: os.environ.get(k) for k in ('OMP_NUM_THREADS', 'OPENBLAS_NUM_THREADS', 'MKL_NUM_THREADS')}
+        for k in saved:
+            os.environ[k] = '1'
+        try:
+            ctx = mp.get_context('spawn')
+            with ctx.Pool(workers) as pool:
+                res = pool.starmap(run_trajectory, [(prob, seed, i) for i in trajs],
+                                   chunksize=max(1, n // (4 * workers)))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
     sign = np.array([r[0] for r in res], dtype=np.int8)
     lnabs = np.array([r[1] for r in res], dtype=np.float64)
     flags = np.array([r[2] for r in res], dtype=np.uint8)
