@@ -59,10 +59,18 @@ extern "C" {
 #define MCTRG_FLAG_NOCONV       16u  /* a Jacobi SVD of this trajectory hit the sweep cap */
 
 /* ---- arithmetic of the contraction ------------------------------------ *
- * FP64: every step in FP64.  TF32 / BF16: the plaquette contraction runs on
- * the tensor cores with FP32 accumulation and per-tensor scaling; the SVD
- * result and the sampling probabilities stay FP64-accurate. */
-typedef enum { MCTRG_FP64 = 0, MCTRG_TF32 = 1, MCTRG_BF16 = 2 } mctrg_precision;
+ * FP64: every step in FP64.  TF32 / BF16: the plaquette GEMM runs on the
+ * tensor cores (tcgen05) with FP32 accumulation; each tensor's two operands
+ * are scaled by their largest magnitude before rounding and the product is
+ * scaled back (per-step scaling).  The X3 variants keep the rounding residual
+ * of each operand and add the two cross products (three passes), which
+ * squares the operand rounding error.  The SVD and the sampling
+ * probabilities stay FP64 in every mode; at a level whose matrices come from
+ * the tensor cores, singular values below min(sqrt(n) u, 1/64) s_1 (u the
+ * operand unit roundoff of the mode) are that arithmetic's noise and count
+ * as zeros.  Levels whose GEMM shape the tensor-core kernel does not cover
+ * (matrix side other than 256) use the FP64 GEMM and the FP64 threshold. */
+typedef enum { MCTRG_FP64 = 0, MCTRG_TF32 = 1, MCTRG_BF16 = 2, MCTRG_TF32X3 = 3, MCTRG_BF16X3 = 4 } mctrg_precision;
 
 typedef struct {
     int device;               /* CUDA device ordinal                                   */

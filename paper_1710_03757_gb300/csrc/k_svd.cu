@@ -15,10 +15,11 @@
 // batch keeps L2-resident (one matrix per SM).  Stopping rule: a sweep with no
 // rotation, where a pair is rotated iff |b_p . b_q| > n_pad 2^-53 |b_p| |b_q|
 // (Demmel and Veselic 1992).  Row norms are recomputed exactly at the start
-// of every sweep and at the end.  Rows whose norm is below 2^-53 |M|_F are
-// rounding noise (they always end below the sampler's zero threshold
-// n 2^-52 s_1): each sweep pairs only the remaining active rows, so a
-// rank-r matrix costs O(r^2 n) per sweep instead of O(n^3).
+// of every sweep and at the end.  Rows whose norm is below (u/2) |M|_F, u the
+// unit roundoff of the arithmetic that produced M (2^-52 for FP64), are
+// rounding noise (they always end below the sampler's zero threshold): each
+// sweep pairs only the remaining active rows, so a rank-r matrix costs
+// O(r^2 n) per sweep instead of O(n^3).
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -35,6 +36,7 @@ static __device__ __forceinline__ double group_sum(double v, int G) {
 
 __global__ void k_jacobi(JacobiArgs a, int use_smem, int G) {
   extern __shared__ double smem[];
+  const double nu = a.noise_u > 0.0 ? a.noise_u : 0x1.0p-52;
   __shared__ int s_rot;
   const int mat = blockIdx.x;
   const int n = a.n, np = a.n_pad;
@@ -68,7 +70,7 @@ __global__ void k_jacobi(JacobiArgs a, int use_smem, int G) {
       if (sweep == 0) {                       // |M|_F^2 is invariant under the rotations
         double f = 0.0;
         for (int r = 0; r < np; ++r) f += nrm[r];
-        s_thr2 = f * 0x1.0p-106;
+        s_thr2 = f * (0.25 * nu * nu);
       }
       int na = 0;
       for (int r = 0; r < np; ++r)
@@ -164,7 +166,7 @@ __global__ void k_jacobi(JacobiArgs a, int use_smem, int G) {
   if (threadIdx.x == 0) {
     double s1 = sg[0];
     if (a.lns1) a.lns1[mat] = s1 > 0.0 ? log(s1) : -INFINITY;
-    const double tau = (double)n * 0x1.0p-52 * s1;
+    const double tau = (a.zero_rel > 0.0 ? a.zero_rel : (double)n * 0x1.0p-52) * s1;
     int cnt = 0;
     for (int r = 0; r < np; ++r) cnt += sg[r] > tau;
     a.nnz[mat] = s1 > 0.0 ? cnt : 0;
@@ -324,6 +326,7 @@ __device__ void qrcp_rows(double* A, int n, int np, int* colperm, double* cn, do
 template <int PW>
 __global__ void __launch_bounds__(512) k_jacobi_warp(JacobiArgs a, int use_smem) {
   extern __shared__ double smem[];
+  const double nu = a.noise_u > 0.0 ? a.noise_u : 0x1.0p-52;
   __shared__ int s_rot, s_na;
   __shared__ double s_thr2;
   constexpr int LOGPW = PW == 1 ? 0 : PW == 2 ? 1 : PW == 4 ? 2 : PW == 8 ? 3 : PW == 16 ? 4 : 5;
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(512) k_jacobi_warp(JacobiArgs a, int use_smem)
       if (sweep == 0) {
         double f = 0.0;
         for (int r = 0; r < np; ++r) f += nrm[r];
-        s_thr2 = f * 0x1.0p-106;
+        s_thr2 = f * (0.25 * nu * nu);
       }
       int na = 0;
       for (int r = 0; r < np; ++r)
@@ -524,7 +527,7 @@ __global__ void __launch_bounds__(512) k_jacobi_warp(JacobiArgs a, int use_smem)
   if (threadIdx.x == 0) {
     const double s1 = sg[0];
     if (a.lns1) a.lns1[mat] = s1 > 0.0 ? log(s1) : -INFINITY;
-    const double tau = (double)n * 0x1.0p-52 * s1;
+    const double tau = (a.zero_rel > 0.0 ? a.zero_rel : (double)n * 0x1.0p-52) * s1;
     int cnt = 0;
     for (int r = 0; r < np; ++r) cnt += sg[r] > tau;
     a.nnz[mat] = s1 > 0.0 ? cnt : 0;

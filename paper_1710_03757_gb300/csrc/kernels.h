@@ -20,6 +20,11 @@ struct JacobiArgs {
   uint32_t* mflags;    // [S] |= FLAG_NOCONV when the sweep cap was hit; may be null
   int n, n_pad, S;
   int max_sweeps;
+  // Noise level of the arithmetic that produced M: singular values at or
+  // below zero_rel * s_1 count as zeros (nnz), and rows below
+  // (noise_u / 2) |M|_F are left out of the sweeps.  0 means FP64:
+  // zero_rel = n 2^-52, noise_u = 2^-52.
+  double zero_rel, noise_u;
 };
 cudaError_t launch_jacobi(const JacobiArgs& a, cudaStream_t st);
 

@@ -18,6 +18,7 @@
 #include "../../include/mctrg.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "kernels_tc.h"
 #include "mctrg_internal.h"
 
 using namespace mctrg;
@@ -75,7 +76,7 @@ extern "C" int mctrg_options_default(mctrg_options* opt) {
 
 extern "C" int mctrg_create(const mctrg_options* opt, mctrg_ctx_t* out) {
   if (!opt || !out) return MCTRG_EINVAL;
-  if (opt->precision < MCTRG_FP64 || opt->precision > MCTRG_BF16) return MCTRG_EINVAL;
+  if (opt->precision < MCTRG_FP64 || opt->precision > MCTRG_BF16X3) return MCTRG_EINVAL;
   *out = nullptr;
   int ndev = 0;
   CK(cudaGetDeviceCount(&ndev));
@@ -161,7 +162,8 @@ void mctrg_ctx::release_all() {
   event_pool.clear();
   DevBuf* all[] = {&T0, &shM, &shW, &shSig, &shPerm, &shNnz, &shLns1, &shU, &shH, &Hbuf[0], &Hbuf[1],
                    &Mb, &Wb, &Xb, &Yb, &sigb, &permb, &nnzb, &ilns1, &iflags, &lnacc, &tflags,
-                   &scratch, &o_lnabs, &o_sign, &o_flags, &o_tflags, &stats};
+                   &scratch, &o_lnabs, &o_sign, &o_flags, &o_tflags, &stats, &tcXh, &tcYh, &tcXl,
+                   &tcYl, &tcScale, &tcErr};
   for (DevBuf* b : all) b->release();
 }
 
@@ -364,6 +366,17 @@ void finish_estimate(mctrg_estimate* e) {
 }
 }  // namespace mctrg
 
+// Unit roundoff of the tensor-core operands of a precision mode.
+static double tc_unit_roundoff(int prec) {
+  switch (prec) {
+    case MCTRG_TF32: return 0x1.0p-11;
+    case MCTRG_BF16: return 0x1.0p-8;
+    case MCTRG_TF32X3: return 0x1.0p-22;
+    case MCTRG_BF16X3: return 0x1.0p-17;
+    default: return 0x1.0p-52;
+  }
+}
+
 int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_out, int8_t* sign_out,
                    uint8_t* flags_out, mctrg_estimate* est) {
   CK(o_lnabs.ensure(sizeof(double) * n));
@@ -415,6 +428,23 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
     CK(permb.ensure(sizeof(int) * std::max<size_t>(max_np, 1)));
     CK(nnzb.ensure(sizeof(int) * std::max<int64_t>(S, 1)));
     CK(scratch.ensure(sizeof(double) * max_scr));
+    // tensor-core operands (mixed precision): per item X and Yt rounded, with scales
+    const int prec = opt.precision;
+    const int tc_kind = (prec == MCTRG_TF32 || prec == MCTRG_TF32X3) ? 0 : 1;
+    const int tc_passes = (prec == MCTRG_TF32X3 || prec == MCTRG_BF16X3) ? 3 : 1;
+    const size_t tc_esize = tc_kind == 0 ? 4 : 2;
+    if (prec != MCTRG_FP64) {
+      const size_t elems = std::max<size_t>(max_xy, 1);
+      CK(tcXh.ensure(tc_esize * elems));
+      CK(tcYh.ensure(tc_esize * elems));
+      if (tc_passes == 3) {
+        CK(tcXl.ensure(tc_esize * elems));
+        CK(tcYl.ensure(tc_esize * elems));
+      }
+      CK(tcScale.ensure(sizeof(double) * 2 * std::max<int64_t>(S, 1)));
+      CK(tcErr.ensure(sizeof(uint32_t)));
+      CK(cudaMemsetAsync(tcErr.p, 0, sizeof(uint32_t), st));
+    }
     for (int64_t c0 = 0; c0 < n; c0 += B) {
       const int64_t Bc = std::min(B, n - c0);
       const uint64_t traj0 = first_traj + (uint64_t)c0;
@@ -454,17 +484,44 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
           const double D2 = (double)p.kc * p.kc, dd = p.D;
           CK(timed(MCTRG_K_FORM_XY, Si, Si * 4.0 * D2 * dd * dd * dd,
                    8.0 * Si * (4.0 * p.kc * dd * dd + 2.0 * D2 * dd * dd), [&] { return launch_form_xy(xa, st); }));
-          GemmArgs gm{};
-          gm.X = Xb.as<double>(); gm.Yt = Yb.as<double>(); gm.M = Mb.as<double>(); gm.D = a.D;
-          gm.K = p.D * p.D; gm.c0 = i0; gm.n_items = Si; gm.Nnew = a.N; gm.L = L; gm.level_new = k;
-          gm.fixed_parity = -1;
-          CK(timed(MCTRG_K_GEMM, Si, Si * 2.0 * a.n * a.n * gm.K, 8.0 * Si * (2.0 * a.n * gm.K + (double)a.n * a.n),
-                   [&] { return launch_gemm_f64(gm, st); }));
+          const int Kd = p.D * p.D;
+          const bool used_tc = prec != MCTRG_FP64 && gemm_tc_supported(a.n, Kd, tc_kind);
+          if (used_tc) {
+            // tensor cores: scale and round the operands, then tcgen05 GEMM
+            double* sX = tcScale.as<double>();
+            double* sY = sX + Si;
+            const int64_t per = (int64_t)a.n * Kd;
+            CK(timed(MCTRG_K_FORM_XY, Si, 0.0, Si * per * (16.0 + 2.0 * tc_esize * tc_passes), [&] {
+              cudaError_t e = launch_convert_scaled(Xb.as<double>(), per, Si, tc_kind, tcXh.p,
+                                                    tc_passes == 3 ? tcXl.p : nullptr, sX, st);
+              if (e != cudaSuccess) return e;
+              return launch_convert_scaled(Yb.as<double>(), per, Si, tc_kind, tcYh.p,
+                                           tc_passes == 3 ? tcYl.p : nullptr, sY, st); }));
+            GemmTcArgs ga{};
+            ga.M = Mb.as<double>(); ga.D = a.D; ga.n = a.n; ga.K = Kd; ga.c0 = i0; ga.n_items = Si;
+            ga.Nnew = a.N; ga.L = L; ga.level_new = k; ga.fixed_parity = -1; ga.scaleX = sX; ga.scaleY = sY;
+            ga.passes = tc_passes; ga.err = tcErr.as<uint32_t>();
+            CK(timed(MCTRG_K_GEMM, Si, Si * 2.0 * a.n * a.n * Kd,
+                     Si * (2.0 * a.n * Kd * tc_esize * tc_passes + 8.0 * a.n * a.n), [&] {
+              return launch_gemm_tc(ga, tc_kind, tcXh.p, tcYh.p, tcXl.p, tcYl.p, st); }));
+          } else {
+            GemmArgs gm{};
+            gm.X = Xb.as<double>(); gm.Yt = Yb.as<double>(); gm.M = Mb.as<double>(); gm.D = a.D;
+            gm.K = Kd; gm.c0 = i0; gm.n_items = Si; gm.Nnew = a.N; gm.L = L; gm.level_new = k;
+            gm.fixed_parity = -1;
+            CK(timed(MCTRG_K_GEMM, Si, Si * 2.0 * a.n * a.n * gm.K, 8.0 * Si * (2.0 * a.n * gm.K + (double)a.n * a.n),
+                     [&] { return launch_gemm_f64(gm, st); }));
+          }
           JacobiArgs ja{};
           ja.M = Mb.as<double>(); ja.W = Wb.as<double>(); ja.sig = sigb.as<double>();
           ja.perm = permb.as<int>(); ja.lns1 = ilns1.as<double>() + i0; ja.nnz = nnzb.as<int>();
           ja.mflags = iflags.as<uint32_t>() + i0; ja.n = a.n; ja.n_pad = a.n_pad; ja.S = (int)Si;
           ja.max_sweeps = opt.max_sweeps;
+          if (used_tc) {
+            const double u = tc_unit_roundoff(prec);
+            ja.noise_u = u;
+            ja.zero_rel = std::min(std::sqrt((double)a.n) * u, 1.0 / 64.0);
+          }
           const double nn = a.n;
           CK(timed(MCTRG_K_JACOBI, Si, Si * ((8.0 / 3.0) * nn * nn * nn + 4.0 * nn * nn * a.kc),
                    8.0 * Si * (nn * nn + (double)a.n_pad * nn + 1.5 * a.n_pad), [&] { return launch_jacobi(ja, st); }));
@@ -507,8 +564,12 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
   if (lnabs_out) CK(cudaMemcpyAsync(lnabs_out, o_lnabs.p, sizeof(double) * n, cudaMemcpyDefault, st));
   if (sign_out) CK(cudaMemcpyAsync(sign_out, o_sign.p, (size_t)n, cudaMemcpyDefault, st));
   if (flags_out) CK(cudaMemcpyAsync(flags_out, o_flags.p, (size_t)n, cudaMemcpyDefault, st));
+  uint32_t tc_err = 0;
+  if (opt.precision != MCTRG_FP64 && tcErr.p)
+    CK(cudaMemcpyAsync(&tc_err, tcErr.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   resolve_events();
+  if (tc_err) return MCTRG_ECUDA;   // a tensor-core pipeline wait expired
   finalize_estimate(hs, n, est);
   // any trajectory whose SVD hit the sweep cap
   if (est->status == MCTRG_OK && any_noconv(n)) est->status = MCTRG_ENOCONV;

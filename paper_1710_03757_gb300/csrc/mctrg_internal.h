@@ -47,6 +47,7 @@ struct mctrg_ctx {
   mctrg::DevBuf T0, shM, shW, shSig, shPerm, shNnz, shLns1, shU, shH;
   mctrg::DevBuf Hbuf[2], Mb, Wb, Xb, Yb, sigb, permb, nnzb, ilns1, iflags, lnacc, tflags, scratch;
   mctrg::DevBuf o_lnabs, o_sign, o_flags, o_tflags, stats;
+  mctrg::DevBuf tcXh, tcYh, tcXl, tcYl, tcScale, tcErr;   // tensor-core operands
 
   // per-kernel-class statistics (MCTRG_K_*)
   mctrg_kernel_stat kstat[MCTRG_K_COUNT]{};

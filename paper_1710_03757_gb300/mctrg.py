@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libmctrg.so")
 MCTRG_OK, MCTRG_EINVAL, MCTRG_ENOMEM, MCTRG_ENOCONV, MCTRG_EDOMAIN = 0, -1, -2, -3, -4
 MCTRG_ECUDA, MCTRG_ESTATE, MCTRG_ETIMEDOUT, MCTRG_EAGAIN, MCTRG_EUNREACHABLE = -5, -6, -7, -8, -9
 MCTRG_ENOTFOUND = -10
-MCTRG_FP64, MCTRG_TF32, MCTRG_BF16 = 0, 1, 2
+MCTRG_FP64, MCTRG_TF32, MCTRG_BF16, MCTRG_TF32X3, MCTRG_BF16X3 = 0, 1, 2, 3, 4
 FLAG_SPLIT_CLUSTER, FLAG_DRAW_TIE, FLAG_TINY_KEPT, FLAG_NOCONV = 1, 2, 4, 16
 
 # every symbol the headers declare (checked by the CPU test suite)

@@ -1,0 +1,59 @@
+"""Mixed precision (the contraction on the tensor cores, SVD and sampling in
+FP64): every result is compared with the FP64 path on the same trajectories.
+
+TF32X3 (error-compensated TF32, three tcgen05 passes) must stay within 1e-6
+of FP64 in the median per-trajectory ln Z and in the estimate; the single-pass
+modes are held to looser bounds that document their error."""
+import numpy as np
+import pytest
+
+from paper_1710_03757_gb300 import build, mctrg
+from paper_1710_03757_gb300.workloads import generic_tensor
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+
+
+def run(prec, L=32, chi=16, n=64, seed=7, beta=0.44, T0=None):
+    ctx = mctrg.mctrg_create(mctrg.make_options(precision=prec))
+    try:
+        s = (mctrg.mctrg_init_lattice(ctx, beta, 0.0, L, chi) if T0 is None
+             else mctrg.mctrg_init_tensor(ctx, T0, T0.shape[0], L, chi))
+        assert s == 0
+        ln = np.zeros(n)
+        sg = np.zeros(n, np.int8)
+        st, est = mctrg.mctrg_run(ctx, n, seed, 0, ln, sg, None)
+        return st, est, ln, sg
+    finally:
+        mctrg.mctrg_destroy(ctx)
+
+
+@pytest.fixture(scope="module")
+def fp64_ref():
+    return run(mctrg.MCTRG_FP64)
+
+
+@pytest.mark.parametrize("prec,med_tol,est_tol", [(mctrg.MCTRG_TF32X3, 1e-6, 1e-6),
+                                                   (mctrg.MCTRG_BF16X3, 1e-5, 1e-5),
+                                                   (mctrg.MCTRG_TF32, 1e-3, 1e-3),
+                                                   (mctrg.MCTRG_BF16, 1e-2, 1e-2)])
+def test_against_fp64(fp64_ref, prec, med_tol, est_tol):
+    st0, est0, ln0, sg0 = fp64_ref
+    st, est, ln, sg = run(prec)
+    assert st == mctrg.MCTRG_OK, mctrg.mctrg_strerror(st)
+    assert np.mean(sg == sg0) >= 0.95
+    err = np.abs(ln - ln0) / np.abs(ln0)
+    assert np.median(err) <= med_tol, np.median(err)
+    assert abs(est.ln_mean_Z - est0.ln_mean_Z) / abs(est0.ln_mean_Z) <= est_tol
+
+
+def test_generic_tensor_mixed():
+    T0 = generic_tensor(2, seed=8)
+    st0, est0, ln0, _ = run(mctrg.MCTRG_FP64, L=8, chi=16, n=16, T0=T0)
+    st, est, ln, _ = run(mctrg.MCTRG_TF32X3, L=8, chi=16, n=16, T0=T0)
+    assert st == 0 and st0 == 0
+    assert np.median(np.abs(ln - ln0) / np.abs(ln0)) <= 1e-6

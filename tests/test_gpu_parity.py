@@ -100,11 +100,34 @@ def test_shared_memory_jacobi_n64():
 
 
 def test_global_workspace_jacobi_n256():
-    # chi = 16: 256 x 256 matrices, Jacobi rows in the L2-resident workspace
+    # chi = 16: 256 x 256 matrices, QR-preconditioned Jacobi rows in the L2-resident workspace
     T0 = generic_tensor(2, seed=8)
-    gpu = gpu_run(8, 16, 8, 12, T0=T0)
-    orc = run_many(Problem(T0, 8, 16), 12, 0, 8, workers=4)
+    gpu = gpu_run(8, 16, 32, 12, T0=T0)
+    orc = run_many(Problem(T0, 8, 16), 12, 0, 32, workers=8)
     compare(gpu, orc, min_ok=0.7)
+
+
+@pytest.mark.parametrize("L,beta,h,n", [(16, 0.44, 0.0, 32), (32, 0.40, 0.05, 16)])
+def test_ising_chi16_parity(L, beta, h, n):
+    # the chi of the headline configuration, every distinct level a 256 x 256 SVD
+    seed = seed_for(2) + L
+    gpu = gpu_run(L, 16, n, seed, beta=beta, h=h)
+    orc = run_many(Problem(ising.site_tensor(beta, h), L, 16), seed, 0, n, workers=8)
+    compare(gpu, orc, min_ok=0.5)
+
+
+def test_full_size_L1024_properties():
+    # the headline lattice (1024 x 1024, chi = 16, beta = 0.44, FP64): the oracle cannot
+    # follow it, so check what holds at any size -- counters fix each trajectory whatever
+    # the batch, the sign, and ln Z~ per site against Onsager's free energy
+    a = gpu_run(1024, 16, 2, seed_for(2), beta=0.44)
+    b = gpu_run(1024, 16, 1, seed_for(2), beta=0.44, first=1)
+    assert a[1][1] == b[1][0]
+    assert np.all(a[2] == 1)
+    f = ising.onsager_minus_beta_f(0.44)
+    assert np.all(np.abs(a[1] / 1024 ** 2 - f) < 2e-3)
+    m = gpu_run(1024, 16, 1, seed_for(2), beta=0.44, first=1, precision=mctrg.MCTRG_TF32X3)
+    assert abs(m[1][0] - b[1][0]) / abs(b[1][0]) < 1e-6
 
 
 def test_exact_path_L2():
