@@ -112,6 +112,8 @@ def oracle_rate(wl, seconds_budget=20.0, workers=None):
     Ls = min(L, 32 if chi >= 16 else (64 if chi >= 8 else 256))
     prob = Problem(ising.site_tensor(wl["beta"], wl["h"]), Ls, chi)
     ctx = mp.get_context("spawn")
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"          # one BLAS thread per worker process
     t0 = time.perf_counter()
     done = 0
     with ctx.Pool(workers) as pool:
@@ -163,6 +165,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--traj-per-step", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.traj_per_step:
@@ -188,56 +191,79 @@ def main():
     if dist:
         dist.barrier()
     stream = torch.cuda.Stream()
-    opts = mctrg.make_options(device=local, stream=stream.cuda_stream, precision=wl["precision"], profile=1)
-    ctx = mctrg.mctrg_create(opts)
-    s = mctrg.mctrg_init_lattice(ctx, wl["beta"], wl["h"], wl["L"], wl["chi"])
-    if s != 0:
-        raise RuntimeError("init failed: " + mctrg.mctrg_strerror(s))
     B = wl["traj_per_step"]
     seed = 0x4D435452 + 2
-    ln_d = torch.zeros(B, dtype=torch.float64, device="cuda")
-    sg_d = torch.zeros(B, dtype=torch.int8, device="cuda")
-    fl_d = torch.zeros(B, dtype=torch.uint8, device="cuda")
-    # trajectory counters: rank r, step s covers [ (s * world + r) * B, ... )
-    step_idx = [0]
 
-    def one_step(host=False):
-        first = (step_idx[0] * world + rank) * B
-        step_idx[0] += 1
-        if host:
-            ln, sg, fl = np.zeros(B), np.zeros(B, np.int8), np.zeros(B, np.uint8)
-        else:
-            ln, sg, fl = ln_d, sg_d, fl_d
-        st, est = mctrg.mctrg_run(ctx, B, seed, first, ln, sg, fl)
+    def make_ctx(prec):
+        opts = mctrg.make_options(device=local, stream=stream.cuda_stream, precision=prec, profile=1)
+        c = mctrg.mctrg_create(opts)
+        s = mctrg.mctrg_init_lattice(c, wl["beta"], wl["h"], wl["L"], wl["chi"])
+        if s != 0:
+            raise RuntimeError("init failed: " + mctrg.mctrg_strerror(s))
+        return c
+
+    def first_of(step):
+        # trajectory counters: rank r, step s covers [(s * world + r) * B, ...)
+        return (step * world + rank) * B
+
+    def one_step(c, step, ln, sg, fl):
+        st, est = mctrg.mctrg_run(c, B, seed, first_of(step), ln, sg, fl)
         if st not in (0, mctrg.MCTRG_EDOMAIN, mctrg.MCTRG_ENOCONV):
             raise RuntimeError("run failed: " + mctrg.mctrg_strerror(st))
         return est
 
-    for _ in range(args.warmup):
-        one_step()
-    torch.cuda.synchronize()
-    mctrg.mctrg_reset_kernel_stats(ctx)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ests = []
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            ests.append(one_step())
-        ev1.record(stream)
+    def timed_steps(c, nsteps, warm, step0):
+        """warm untimed steps, then nsteps timed steps; returns ms, estimates, per-step outputs."""
+        outs = [(torch.zeros(B, dtype=torch.float64, device="cuda"), torch.zeros(B, dtype=torch.int8, device="cuda"),
+                 torch.zeros(B, dtype=torch.uint8, device="cuda")) for _ in range(nsteps)]
+        for w in range(warm):
+            one_step(c, step0 + nsteps + 1 + w, *outs[0])   # counters outside the timed range
         torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
+        mctrg.mctrg_reset_kernel_stats(c)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ests = []
+        e0.record(stream)
+        for i in range(nsteps):
+            ests.append(one_step(c, step0 + i, *outs[i]))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        return e0.elapsed_time(e1), ests, outs
+
+    ctx = make_ctx(wl["precision"])
+    with ClockSampler(local) as clk:
+        ms, ests, outs = timed_steps(ctx, args.steps, args.warmup, 0)
     stats = [mctrg.mctrg_kernel_stats(ctx, k) for k in range(mctrg.K_COUNT)]
     launches = int(sum(st_.launches for st_ in stats))
-    # e2e: the public API call a user makes, host result buffers, wall clock
+    # e2e: the public API calls a user makes (create, init, run), host result buffers, wall clock
     t0 = time.perf_counter()
-    for _ in range(max(1, min(args.steps, 2))):
-        one_step(host=True)
-    e2e_s = (time.perf_counter() - t0) / max(1, min(args.steps, 2))
+    c2 = make_ctx(wl["precision"])
+    ln_h, sg_h, fl_h = np.zeros(B), np.zeros(B, np.int8), np.zeros(B, np.uint8)
+    one_step(c2, args.steps, ln_h, sg_h, fl_h)
+    mctrg.mctrg_destroy(c2)
+    e2e_s = time.perf_counter() - t0
+    # the same trajectories with the contraction on the tensor cores (error-compensated TF32)
+    mixed = None
+    if wl["precision"] == 0 and not args.no_mixed:
+        cm = make_ctx(mctrg.MCTRG_TF32X3)
+        ms_m, ests_m, outs_m = timed_steps(cm, args.steps, 1, 0)
+        mctrg.mctrg_destroy(cm)
+        ref = np.concatenate([o[0].cpu().numpy() for o in outs])
+        got = np.concatenate([o[0].cpu().numpy() for o in outs_m])
+        ok = np.isfinite(ref) & np.isfinite(got)
+        rel = np.abs(got[ok] - ref[ok]) / np.abs(ref[ok])
+        em, e64 = mctrg.mctrg_merge_estimates(ests_m), mctrg.mctrg_merge_estimates(ests)
+        mixed = {"precision": "tf32x3 contraction (tcgen05), FP64 SVD and sampling",
+                 "value": B * args.steps * world / (ms_m / 1000.0), "ms_per_step": ms_m / args.steps,
+                 "lnZ_rel_err_per_traj_median": float(np.median(rel)) if rel.size else None,
+                 "lnZ_rel_err_per_traj_max": float(np.max(rel)) if rel.size else None,
+                 "lnZ_abs_err_per_traj_median": float(np.median(np.abs(got[ok] - ref[ok]))) if rel.size else None,
+                 "lnZhat_rel_err": abs(em.ln_mean_Z - e64.ln_mean_Z) / abs(e64.ln_mean_Z)
+                 if np.isfinite(em.ln_mean_Z) and np.isfinite(e64.ln_mean_Z) else None}
     ms_t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -277,10 +303,12 @@ def main():
             "config": {"workload": args.workload, "L": wl["L"], "chi": wl["chi"], "beta": wl["beta"],
                        "h": wl["h"], "trajectories_per_step_per_gpu": B, "parallelism": "replicas%d" % world,
                        "l2": "working set (halves, matrices) far larger than L2; no flush needed"},
-            "e2e": {"value": total_traj / args.steps / e2e_max if e2e_max > 0 else None,
+            "e2e": {"value": B * world / e2e_max if e2e_max > 0 else None,
                     "unit": "trajectories/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": B * (8 + 1 + 1) + 8 * 6,
-                    "note": "mctrg_run with host result buffers; inputs are five scalars passed by value"},
+                    "note": "mctrg_create + mctrg_init_lattice + mctrg_run with host result buffers, wall "
+                            "clock; the inputs are five scalars passed by value (beta, h, L, chi, seed)"},
+            "mixed": mixed,
             "gpu_launches": launches, "roofline": roof, "kernels": kernels,
             "estimate": {"ln_mean_Z": merged.ln_mean_Z, "se_ln_Z": merged.se_ln_Z, "n": merged.n,
                          "ess": merged.ess, "n_flagged": merged.n_flagged},
