@@ -35,6 +35,9 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # FP64 peak of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz = 1.26
 # TFLOP/s (nominal 1.25); a DFMA throughput probe on this machine measured 1.01.
 FP64_NOMINAL_TFLOPS = 1.25
+# DRAM bytes (read + write) of one 256 x 256 matrix in k_jacobi_warp, from the ncu capture
+# summarized in profiles/k_jacobi_warp_n256_ising_L32_chi16.md (2.66 GB for 128 matrices)
+JACOBI_DRAM_BYTES_PER_MATRIX_N256 = 2.658e9 / 128
 
 
 def measured_peaks():
@@ -286,7 +289,10 @@ def main():
         roof = {"bound": "alu", "kernel": mctrg.KERNEL_NAMES[dom], "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": "nominal FP64 (DFMA) rate of GB300; the pool's DFMA probe measured 1.01 TFLOP/s",
-                "traffic": None, "launches": ds.launches, "avg_launch_ms": ds.ms / max(1, ds.launches),
+                "traffic": (JACOBI_DRAM_BYTES_PER_MATRIX_N256 * ds.items / max(1, ds.launches)
+                            if dom == mctrg.K_JACOBI and wl["chi"] == 16 else None),
+                "traffic_note": "bytes per launch, scaled from the per-matrix DRAM bytes of the ncu capture",
+                "launches": ds.launches, "avg_launch_ms": ds.ms / max(1, ds.launches),
                 "alg_flops_per_launch": ds.flops_alg / max(1, ds.launches)}
     else:
         achieved = ds.bytes_alg / (ds.ms / 1000.0) / 1e9 if ds.ms > 0 else 0.0
