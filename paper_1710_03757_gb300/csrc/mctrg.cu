@@ -578,7 +578,9 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
 
 bool mctrg_ctx::any_noconv(int64_t n) {
   std::vector<uint8_t> f((size_t)n);
-  if (cudaMemcpy(f.data(), o_flags.p, (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+  if (cudaMemcpyAsync(f.data(), o_flags.p, (size_t)n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return false;
   for (uint8_t v : f)
     if (v & FLAG_NOCONV) return true;
   return false;
