@@ -136,6 +136,80 @@ def oracle_rate(wl, seconds_budget=20.0, workers=None):
     return rate, workers, desc
 
 
+def measure_serving(mctrg, seconds, rate, seed=0xB0A7 + 5):
+    """Poisson arrivals of estimate jobs into the server; latency percentiles.
+
+    Job mix (small-lattice stand-in of the serving workload): beta uniform in
+    [0.3, 0.6], h in {0, 0.05}, L in {4, 8, 16}, chi in {2, 4}, target standard
+    error of ln Z log-uniform in [1e-2, 1e-1], at most 2^16 trajectories.
+    """
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    srv = mctrg.mctrg_server_create()
+    ids, t0 = [], time.perf_counter()
+    t_next = 0.0
+    try:
+        while t_next < seconds:
+            now = time.perf_counter() - t0
+            if now < t_next:
+                time.sleep(t_next - now)
+            L = int(rng.choice([4, 8, 16]))
+            chi = int(rng.choice([2, 4]))
+            tgt = float(10 ** rng.uniform(-2, -1))
+            st, j = mctrg.mctrg_server_submit(srv, float(rng.uniform(0.3, 0.6)), float(rng.choice([0.0, 0.05])),
+                                              L, chi, tgt, 1 << 16, int(rng.integers(1 << 62)))
+            if st == 0:
+                ids.append(j)
+            t_next += float(rng.exponential(1.0 / rate))
+        lat, traj, unreached = [], 0, 0
+        for j in ids:
+            st, est, l = mctrg.mctrg_server_wait(srv, j, 600.0)
+            lat.append(l)
+            traj += est.n
+            unreached += st == mctrg.MCTRG_EUNREACHABLE
+        wall = time.perf_counter() - t0
+    finally:
+        mctrg.mctrg_server_destroy(srv)
+    lat = np.sort(np.array(lat))
+    return {"offered_jobs_per_s": rate, "jobs": len(ids), "seconds_of_arrivals": seconds,
+            "latency_p50_s": float(lat[len(lat) // 2]) if len(lat) else None,
+            "latency_p99_s": float(lat[min(len(lat) - 1, int(0.99 * len(lat)))]) if len(lat) else None,
+            "trajectories_per_s": traj / wall, "jobs_below_target": len(ids) - unreached,
+            "mix": "beta U[0.3,0.6], h {0,0.05}, L {4,8,16}, chi {2,4}, target SE(ln Z) 1e-2..1e-1 log-uniform"}
+
+
+def measure_uneven(mctrg, n_jobs=32, seed=0xB0A7 + 4):
+    """Jobs of uneven chi and lattice size sharing the device through the server.
+
+    Stand-in of the uneven-batch workload at feasible sizes: chi in {4, 8, 16, 24},
+    L in {8, 16, 32, 64}, beta uniform in [0.3, 0.6], h uniform in [0, 0.1], a fixed
+    number of trajectories each (128-1024), all submitted at once.
+    """
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    srv = mctrg.mctrg_server_create()
+    t0 = time.perf_counter()
+    ids = []
+    try:
+        for _ in range(n_jobs):
+            chi = int(rng.choice([4, 8, 16, 24]))
+            L = int(rng.choice([8, 16, 32, 64] if chi <= 8 else [8, 16, 32]))
+            n = int(rng.integers(128, 1025))
+            st, j = mctrg.mctrg_server_submit(srv, float(rng.uniform(0.3, 0.6)), float(rng.uniform(0, 0.1)),
+                                              L, chi, 1e-12, n, int(rng.integers(1 << 62)))
+            if st == 0:
+                ids.append(j)
+        traj = 0
+        for j in ids:
+            st, est, l = mctrg.mctrg_server_wait(srv, j, 900.0)
+            traj += est.n
+        wall = time.perf_counter() - t0
+    finally:
+        mctrg.mctrg_server_destroy(srv)
+    return {"jobs": len(ids), "trajectories": traj, "seconds": wall, "trajectories_per_s": traj / wall,
+            "mix": "chi {4,8,16,24}, L {8..64}, beta U[0.3,0.6], h U[0,0.1], 128-1024 trajectories each"}
+
+
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return
@@ -169,6 +243,9 @@ def main():
     ap.add_argument("--traj-per-step", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--no-uneven", action="store_true")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.traj_per_step:
@@ -320,6 +397,16 @@ def main():
                          "ess": merged.ess, "n_flagged": merged.n_flagged},
             "clocks": clk.summary()}
     mctrg.mctrg_destroy(ctx)
+    if args.serve_seconds > 0:
+        try:
+            line["serve"] = measure_serving(mctrg, args.serve_seconds, args.serve_rate)
+        except Exception as e:
+            line["serve"] = {"error": repr(e)[:200]}
+    if not args.no_uneven:
+        try:
+            line["uneven_batch"] = measure_uneven(mctrg)
+        except Exception as e:
+            line["uneven_batch"] = {"error": repr(e)[:200]}
     if not args.no_cpu_baseline:
         try:
             r, cores, desc = oracle_rate(wl)
