@@ -222,23 +222,27 @@ void mctrg_destroy(mctrg_ctx_t ctx);
 const char* mctrg_strerror(int status);
 
 /* ---- serving: continuous batching of estimate jobs -------------------- *
- * A server owns one device and a worker thread.  Jobs (beta, h, L, chi,
- * target standard error of ln Z) arrive with mctrg_server_submit, are admitted
- * when their device footprint fits the free budget, and advance in rounds of
- * trajectories that share the device with every other admitted job until
- * their target error or max_samples is reached.  Trajectory i of a job uses
- * counter i under the job's seed, so its result is the same alone and in any
- * mix. */
+ * A server owns one device and a fixed pool of workers, each with its own
+ * stream and a persistent context holding an equal share of the device
+ * memory budget.  Jobs (beta, h, L, chi, target standard error of ln Z)
+ * arrive with mctrg_server_submit at any time; a free worker takes the oldest
+ * queued job and advances it in rounds of trajectories (chunked to fit the
+ * worker's memory) until its target error or max_samples is reached, so the
+ * kernels of all running jobs share the device and a finished job's worker
+ * starts the next one at once, reusing its device buffers.  Trajectory i of a
+ * job uses counter i under the job's seed, so its result is the same alone
+ * and in any mix. */
 typedef struct mctrg_server* mctrg_server_t;
 
 int mctrg_server_create(const mctrg_options* opt, mctrg_server_t* out);
 /* Non-blocking.  target_se_lnZ > 0; max_samples >= 1.  Returns EUNREACHABLE
- * at once when the job cannot fit or its projected cost is unbounded. */
+ * at once when even one trajectory of the job cannot fit a worker's memory. */
 int mctrg_server_submit(mctrg_server_t srv, double beta, double h, int L, int chi,
                         double target_se_lnZ, int64_t max_samples, uint64_t seed,
                         uint64_t* job_id);
 /* EAGAIN until the job is done; then fills *est and *latency_s (submit to
- * completion, seconds) and forgets the job. */
+ * completion, seconds) and forgets the job.  Returns OK when the target error
+ * was reached, EUNREACHABLE (est still filled) when max_samples ran out first. */
 int mctrg_server_poll(mctrg_server_t srv, uint64_t job_id, mctrg_estimate* est, double* latency_s);
 /* Blocks up to timeout_s; ETIMEDOUT if the job is still running. */
 int mctrg_server_wait(mctrg_server_t srv, uint64_t job_id, double timeout_s,

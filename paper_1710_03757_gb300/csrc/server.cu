@@ -1,11 +1,13 @@
 // Serving loop: continuous batching of Monte Carlo TRG estimate jobs.
 //
 // Jobs (beta, h, L, chi, target standard error of ln Z) arrive at any time.
-// An admission thread admits queued jobs in arrival order whenever their
-// device footprint fits the memory not held by running jobs; each admitted
-// job then advances in rounds of trajectories on its own context and CUDA
-// stream, so the kernels of all running jobs share the device concurrently,
-// and a finished job frees its memory for the next queued one.  A job's
+// A fixed pool of workers, each with its own CUDA stream and a persistent
+// context holding an equal share of the device-memory budget, takes queued
+// jobs in arrival order as soon as a worker is free; a job advances in rounds
+// of trajectories (chunked to fit its worker's memory), so the kernels of all
+// running jobs share the device concurrently, and a worker that finishes a
+// job immediately starts the next queued one with the buffers it already
+// holds.  A job's
 // trajectory i always uses Philox counter i under the job's seed and its
 // rounds merge through the sufficient statistics of mctrg_merge_estimates,
 // so its result is the same alone and in any mix.
@@ -37,7 +39,6 @@ struct Job {
   int state = 0;            // 0 queued, 1 running, 2 done
   int status = MCTRG_OK;
   mctrg_estimate est{};
-  std::thread th;
 };
 
 // Upper bound of the device bytes of a job that runs rounds of R trajectories:
@@ -66,36 +67,27 @@ size_t job_footprint(int L, int chi, int64_t R) {
 
 struct mctrg_server {
   mctrg_options opt{};
-  size_t budget = 0, used = 0;
-  int max_active = 64;
+  size_t budget = 0;                // whole server
+  size_t worker_budget = 0;         // each worker context
+  int n_workers = 16;
   std::mutex mu;
-  std::condition_variable cv;       // admission thread wakes on submit / finish / stop
+  std::condition_variable cv;       // workers wake on submit / stop
   std::condition_variable done_cv;  // waiters wake when a job finishes
   std::deque<Job*> queue;
   std::map<uint64_t, Job*> jobs;
-  int active = 0;
   bool stop = false;
   uint64_t next_id = 1;
-  std::thread admitter;
+  std::vector<std::thread> workers;
 
   static constexpr int64_t kRound0 = 256;   // first round; later rounds double up to kRoundMax
   static constexpr int64_t kRoundMax = 8192;
 
-  void run_job(Job* j) {
-    cudaSetDevice(opt.device);
-    cudaStream_t st = nullptr;
-    int status = MCTRG_OK;
+  // One job on a worker's persistent context: rounds of trajectories until the
+  // target standard error of ln Z or max_samples is reached.
+  void run_job(mctrg_ctx_t ctx, Job* j) {
+    int status = mctrg_init_lattice(ctx, j->beta, j->h, j->L, j->chi);
     mctrg_estimate total{};
     bool have = false;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) status = MCTRG_ECUDA;
-    mctrg_ctx_t ctx = nullptr;
-    if (status == MCTRG_OK) {
-      mctrg_options o = opt;
-      o.cuda_stream = st;
-      o.hbm_budget_bytes = j->footprint;
-      status = mctrg_create(&o, &ctx);
-    }
-    if (status == MCTRG_OK) status = mctrg_init_lattice(ctx, j->beta, j->h, j->L, j->chi);
     int64_t done = 0, round = kRound0;
     while (status == MCTRG_OK && done < j->max_samples) {
       const int64_t R = std::min(round, j->max_samples - done);
@@ -113,34 +105,50 @@ struct mctrg_server {
     }
     if (status == MCTRG_OK && !(total.status == MCTRG_OK && total.se_ln_Z <= j->target))
       status = MCTRG_EUNREACHABLE;
-    if (ctx) mctrg_destroy(ctx);
-    if (st) cudaStreamDestroy(st);
     std::lock_guard<std::mutex> lk(mu);
     j->est = total;
     j->status = status;
     j->t_done = Clock::now();
     j->state = 2;
-    used -= j->footprint;
-    --active;
-    cv.notify_all();
     done_cv.notify_all();
   }
 
-  void admission_loop() {
-    std::unique_lock<std::mutex> lk(mu);
-    while (!stop) {
-      bool admitted = false;
-      while (!queue.empty() && active < max_active && used + queue.front()->footprint <= budget) {
-        Job* j = queue.front();
-        queue.pop_front();
-        used += j->footprint;
-        ++active;
-        j->state = 1;
-        j->th = std::thread(&mctrg_server::run_job, this, j);
-        admitted = true;
-      }
-      if (!admitted) cv.wait(lk);
+  // A worker owns one stream and one context for its whole life, so jobs reuse
+  // device buffers instead of allocating and freeing them (cudaFree waits for
+  // the whole device, which would serialize every running job).
+  void worker_loop() {
+    cudaSetDevice(opt.device);
+    cudaStream_t st = nullptr;
+    mctrg_ctx_t ctx = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) {
+      mctrg_options o = opt;
+      o.cuda_stream = st;
+      o.hbm_budget_bytes = worker_budget;
+      o.profile = 0;
+      if (mctrg_create(&o, &ctx) != MCTRG_OK) ctx = nullptr;
     }
+    for (;;) {
+      Job* j = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return stop || !queue.empty(); });
+        if (stop) break;
+        j = queue.front();
+        queue.pop_front();
+        j->state = 1;
+      }
+      if (ctx) {
+        run_job(ctx, j);
+      } else {
+        std::lock_guard<std::mutex> lk(mu);
+        j->status = MCTRG_ECUDA;
+        j->t_done = Clock::now();
+        j->state = 2;
+        done_cv.notify_all();
+      }
+    }
+    if (ctx) mctrg_destroy(ctx);
+    if (st) cudaStreamDestroy(st);
   }
 };
 
@@ -159,7 +167,8 @@ extern "C" int mctrg_server_create(const mctrg_options* opt, mctrg_server_t* out
     s->opt.hbm_budget_bytes = (size_t)(0.8 * (double)fr);
   }
   s->budget = s->opt.hbm_budget_bytes;
-  s->admitter = std::thread(&mctrg_server::admission_loop, s);
+  s->worker_budget = s->budget / (size_t)s->n_workers;
+  for (int w = 0; w < s->n_workers; ++w) s->workers.emplace_back(&mctrg_server::worker_loop, s);
   *out = s;
   return MCTRG_OK;
 }
@@ -175,8 +184,10 @@ extern "C" int mctrg_server_submit(mctrg_server_t s, double beta, double h, int 
   Job* j = new Job();
   j->beta = beta; j->h = h; j->L = L; j->chi = chi; j->target = target_se_lnZ;
   j->max_samples = max_samples; j->seed = seed;
-  j->footprint = job_footprint(L, chi, std::min<int64_t>(max_samples, mctrg_server::kRoundMax));
-  if (j->footprint > s->budget) {   // can never be admitted
+  // a job runs in chunks that fit a worker's share of the memory; if even one
+  // trajectory cannot fit there, it can never run
+  j->footprint = job_footprint(L, chi, 1);
+  if (j->footprint > s->worker_budget) {
     delete j;
     return MCTRG_EUNREACHABLE;
   }
@@ -197,7 +208,6 @@ static int take_result(mctrg_server* s, std::map<uint64_t, Job*>::iterator it, m
   if (latency_s) *latency_s = std::chrono::duration<double>(j->t_done - j->t_submit).count();
   const int st = j->status;
   s->jobs.erase(it);
-  if (j->th.joinable()) j->th.join();
   delete j;
   return st;
 }
@@ -239,15 +249,9 @@ extern "C" void mctrg_server_destroy(mctrg_server_t s) {
     s->queue.clear();
     s->cv.notify_all();
   }
-  if (s->admitter.joinable()) s->admitter.join();
-  std::map<uint64_t, Job*> rest;
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    rest.swap(s->jobs);
-  }
-  for (auto& kv : rest) {
-    if (kv.second->th.joinable()) kv.second->th.join();
-    delete kv.second;
-  }
+  for (std::thread& t : s->workers)
+    if (t.joinable()) t.join();   // running jobs finish their current job first
+  for (auto& kv : s->jobs) delete kv.second;
+  s->jobs.clear();
   delete s;
 }
