@@ -136,46 +136,57 @@ def oracle_rate(wl, seconds_budget=20.0, workers=None):
     return rate, workers, desc
 
 
-def measure_serving(mctrg, seconds, rate, seed=0xB0A7 + 5):
-    """Poisson arrivals of estimate jobs into the server; latency percentiles.
+def _serve_mix(rng):
+    return (float(rng.uniform(0.3, 0.6)), float(rng.choice([0.0, 0.05])), int(rng.choice([4, 8, 16])),
+            int(rng.choice([2, 4])), float(10 ** rng.uniform(-2, -1)), 1 << 16, int(rng.integers(1 << 62)))
+
+
+def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5):
+    """Continuous batching under Poisson arrivals at a stated fraction of capacity.
 
     Job mix (small-lattice stand-in of the serving workload): beta uniform in
     [0.3, 0.6], h in {0, 0.05}, L in {4, 8, 16}, chi in {2, 4}, target standard
-    error of ln Z log-uniform in [1e-2, 1e-1], at most 2^16 trajectories.
+    error of ln Z log-uniform in [1e-2, 1e-1], at most 2^16 trajectories.  The
+    server's capacity (trajectories/s and trajectories per job) is measured
+    first on a burst of 64 jobs from the same mix; arrivals then come at
+    `load` times the job rate that capacity sustains.
     """
     import numpy as np
     rng = np.random.default_rng(seed)
     srv = mctrg.mctrg_server_create()
-    ids, t0 = [], time.perf_counter()
-    t_next = 0.0
     try:
+        t0 = time.perf_counter()
+        burst = [mctrg.mctrg_server_submit(srv, *_serve_mix(rng))[1] for _ in range(64)]
+        traj = sum(mctrg.mctrg_server_wait(srv, j, 900.0)[1].n for j in burst)
+        cap = traj / (time.perf_counter() - t0)
+        rate = load * cap / (traj / 64.0)
+        ids, lat, n_traj, reached = [], [], 0, 0
+        t0 = time.perf_counter()
+        t_next = 0.0
         while t_next < seconds:
             now = time.perf_counter() - t0
             if now < t_next:
                 time.sleep(t_next - now)
-            L = int(rng.choice([4, 8, 16]))
-            chi = int(rng.choice([2, 4]))
-            tgt = float(10 ** rng.uniform(-2, -1))
-            st, j = mctrg.mctrg_server_submit(srv, float(rng.uniform(0.3, 0.6)), float(rng.choice([0.0, 0.05])),
-                                              L, chi, tgt, 1 << 16, int(rng.integers(1 << 62)))
+            st, j = mctrg.mctrg_server_submit(srv, *_serve_mix(rng))
             if st == 0:
                 ids.append(j)
             t_next += float(rng.exponential(1.0 / rate))
-        lat, traj, unreached = [], 0, 0
         for j in ids:
-            st, est, l = mctrg.mctrg_server_wait(srv, j, 600.0)
+            st, est, l = mctrg.mctrg_server_wait(srv, j, 900.0)
             lat.append(l)
-            traj += est.n
-            unreached += st == mctrg.MCTRG_EUNREACHABLE
+            n_traj += est.n
+            reached += st == 0
         wall = time.perf_counter() - t0
     finally:
         mctrg.mctrg_server_destroy(srv)
     lat = np.sort(np.array(lat))
-    return {"offered_jobs_per_s": rate, "jobs": len(ids), "seconds_of_arrivals": seconds,
+    return {"capacity_trajectories_per_s": cap, "offered_load": load, "offered_jobs_per_s": rate,
+            "jobs": len(ids), "seconds_of_arrivals": seconds,
             "latency_p50_s": float(lat[len(lat) // 2]) if len(lat) else None,
             "latency_p99_s": float(lat[min(len(lat) - 1, int(0.99 * len(lat)))]) if len(lat) else None,
-            "trajectories_per_s": traj / wall, "jobs_below_target": len(ids) - unreached,
-            "mix": "beta U[0.3,0.6], h {0,0.05}, L {4,8,16}, chi {2,4}, target SE(ln Z) 1e-2..1e-1 log-uniform"}
+            "trajectories_per_s": n_traj / wall, "jobs_reaching_target": reached,
+            "mix": "beta U[0.3,0.6], h {0,0.05}, L {4,8,16}, chi {2,4}, target SE(ln Z) 1e-2..1e-1 "
+                   "log-uniform, max 2^16 trajectories"}
 
 
 def measure_uneven(mctrg, n_jobs=32, seed=0xB0A7 + 4):
@@ -243,8 +254,8 @@ def main():
     ap.add_argument("--traj-per-step", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=8.0)
-    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--no-uneven", action="store_true")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
@@ -399,7 +410,7 @@ def main():
     mctrg.mctrg_destroy(ctx)
     if args.serve_seconds > 0:
         try:
-            line["serve"] = measure_serving(mctrg, args.serve_seconds, args.serve_rate)
+            line["serve"] = measure_serving(mctrg, args.serve_seconds, args.serve_load)
         except Exception as e:
             line["serve"] = {"error": repr(e)[:200]}
     if not args.no_uneven:

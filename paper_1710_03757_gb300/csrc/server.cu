@@ -56,11 +56,12 @@ size_t job_footprint(int L, int chi, int64_t R) {
     const size_t hk = N * 2 * n * kc * 8;
     maxpair = std::max(maxpair, hk + prevh);
     prevh = hk;
-    work = std::max(work, (size_t)(5 * n * n * 8));
+    work = std::max(work, (size_t)(5 * n * n * 8 + (n + 1) * 65 * 8));
     D = kc;
   }
   per_traj += maxpair;
-  return per_traj * (size_t)R + work * 4096 + (64u << 20);
+  // trajectories in flight, one matrix of working space, fixed buffers
+  return per_traj * (size_t)R + work + (64u << 20);
 }
 
 }  // namespace
@@ -76,6 +77,7 @@ struct mctrg_server {
   std::deque<Job*> queue;
   std::map<uint64_t, Job*> jobs;
   bool stop = false;
+  std::atomic<bool> stop_flag{false};   // running jobs stop at their next round
   uint64_t next_id = 1;
   std::vector<std::thread> workers;
 
@@ -90,6 +92,7 @@ struct mctrg_server {
     bool have = false;
     int64_t done = 0, round = kRound0;
     while (status == MCTRG_OK && done < j->max_samples) {
+      if (stop_flag.load(std::memory_order_relaxed)) break;   // server shutting down
       const int64_t R = std::min(round, j->max_samples - done);
       mctrg_estimate e{};
       int s = mctrg_run(ctx, R, j->seed, (uint64_t)done, nullptr, nullptr, nullptr, &e);
@@ -244,6 +247,7 @@ extern "C" void mctrg_server_destroy(mctrg_server_t s) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
+    s->stop_flag.store(true);
     // queued jobs never start
     for (Job* j : s->queue) { s->jobs.erase(j->id); delete j; }
     s->queue.clear();
