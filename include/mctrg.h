@@ -81,7 +81,20 @@ typedef struct {
     int max_chunk;            /* max trajectories per device chunk; 0 = automatic      */
     int profile;              /* 1: time every kernel launch with CUDA events on the
                                  context's stream (see mctrg_kernel_stats)             */
+    int svd;                  /* mctrg_svd_route of the per-trajectory SVDs            */
 } mctrg_options;
+
+/* Route of the per-trajectory SVDs (Sec. II, Eq. exactSVD), both FP64 with
+ * the absolute accuracy of a backward-stable SVD (a few eps |M|):
+ *   JACOBI  QR with column pivoting, then one-sided Jacobi on the rows; its
+ *           cost follows the numerical rank.
+ *   BIDIAG  Householder bidiagonalization, every singular value by bisection
+ *           on Sturm counts of the Golub-Kahan tridiagonal, and right vectors
+ *           of the kept indices only (inverse iteration, back-transformation);
+ *           (8/3) n^3 + O(n^2) flops whatever the rank.
+ *   AUTO    BIDIAG where the matrices can have full rank (n >= 64 and the
+ *           plaquette's inner dimension d^2 >= n / 2), JACOBI elsewhere. */
+typedef enum { MCTRG_SVD_AUTO = 0, MCTRG_SVD_JACOBI = 1, MCTRG_SVD_BIDIAG = 2 } mctrg_svd_route;
 
 /* Estimate of Z from n trajectories (Sec. III Eq. infiniteEnsemble, Sec. V Eq.
  * shrunkDev).  With m = ln_scale = max_i ln|Z~_i| and x_i = sign_i e^{ln|Z~_i| - m}:
@@ -159,10 +172,15 @@ int mctrg_merge_estimates(const mctrg_estimate* parts, int k, mctrg_estimate* ou
  *   FORM_XY  4 D^2 d^3 per tensor
  *   SAMPLE   4 n kc + 2 n^2 kc per tensor (tables and draws; left halves M v)
  *   TRACE    2 D^2 d^2 per trajectory
+ *   BIDIAG   (8/3) n^3 per matrix (Householder bidiagonalization)
+ *   BISECT   4 n per Sturm count, 1 + 44 nnz counts per matrix
+ *   VECTORS  2 n^2 kc + 20 (2n) kc per matrix (back-transformation and
+ *            inverse iteration of the kept vectors)
  * bytes_alg counts each kernel's compulsory global-memory traffic
  * (inputs read once, outputs written once). */
 enum { MCTRG_K_FORM_XY = 0, MCTRG_K_GEMM = 1, MCTRG_K_JACOBI = 2, MCTRG_K_SAMPLE = 3,
-       MCTRG_K_TRACE = 4, MCTRG_K_OTHER = 5, MCTRG_K_COUNT = 6 };
+       MCTRG_K_TRACE = 4, MCTRG_K_OTHER = 5, MCTRG_K_BIDIAG = 6, MCTRG_K_BISECT = 7,
+       MCTRG_K_VECTORS = 8, MCTRG_K_COUNT = 9 };
 typedef struct {
     int64_t launches;
     double ms;          /* summed event-timed duration */
@@ -214,6 +232,21 @@ int mctrg_svd_batched(const double* M, int n, int64_t batch, double* sigma, doub
 #define MCTRG_SVD_NOALLOC_MAX_N 1024
 int mctrg_svd_batched_noalloc(const double* M, int n, int64_t batch, double* sigma, double* vt,
                               int max_sweeps, void* stream);
+
+/* The bidiagonalization route of the same SVD on its own (the route
+ * MCTRG_SVD_BIDIAG of the contexts): Householder bidiagonalization, every
+ * singular value by bisection on Sturm counts of the Golub-Kahan tridiagonal,
+ * and the right vectors of the n_vec largest singular values by inverse
+ * iteration and back-transformation.  M (device, batch*n*n, row-major) is read
+ * only; sigma (device, batch*n) receives the singular values in descending
+ * order (values below n 2^-52 max_ij |B_ij|, B the bidiagonal, are 0);
+ * vt (device, batch*n_vec*n; NULL when n_vec = 0) receives unit right vectors
+ * as rows.  Each value carries an absolute error of a few 2^-52 |M|; vectors
+ * of values closer than 1e-3 |M| to another are an orthonormal basis of their
+ * cluster's subspace.  Allocates and frees its working memory.
+ * 2 <= n <= 768, 0 <= n_vec <= min(32, n).  Errors: EINVAL, ENOMEM, ECUDA. */
+int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, double* sigma, int n_vec,
+                             double* vt, void* stream);
 
 /* Release every resource of the context (NULL is a no-op). */
 void mctrg_destroy(mctrg_ctx_t ctx);

@@ -1,0 +1,491 @@
+// K2, bidiagonalization route: the SVD of a level matrix (Sec. II, Eq. exactSVD)
+// at the flop count of a bidiagonal reduction, (8/3) n^3, instead of the
+// repeated sweeps of one-sided Jacobi, with singular vectors computed only
+// for the indices the sampler keeps.
+//
+//  1. k_bidiag        Householder bidiagonalization M = Q_L B Q_R^T (Golub and
+//                     Kahan 1965), one CTA per matrix; d, e of the upper
+//                     bidiagonal B and the right reflectors kept in place.
+//  2. k_bd_bisect     every singular value of B by bisection on Sturm counts of
+//                     the Golub-Kahan tridiagonal T (zero diagonal, off-
+//                     diagonal d_0 e_0 d_1 e_1 ... d_{n-1}; eigenvalues +-s_i),
+//                     one thread per singular value.  The count is the number
+//                     of sign changes of the leading principal minors P_k of
+//                     T - x I, P_k = -x P_{k-1} - o_{k-2}^2 P_{k-2} (Barth,
+//                     Martin and Wilkinson 1967), with power-of-two rescaling
+//                     against underflow; it is the exact count of a matrix
+//                     within a few ulps of T entrywise, so each value carries
+//                     an absolute error of a few eps |B|, the accuracy class
+//                     of LAPACK's SVD.
+//  (the sampler then chooses the kept indices)
+//  3. k_bd_invit      right singular vectors of B for the kept indices: inverse
+//                     iteration on T - s I (LU with partial pivoting) whose
+//                     eigenvector for +s is (v_0, u_0, v_1, u_1, ...),
+//                     reorthogonalized within clusters of close kept values
+//                     (as LAPACK's dstein), one lane per kept vector.
+//  4. k_bd_backtr     v = Q_R v_B through the stored reflectors, written as
+//                     s v (the scaling of a one-sided Jacobi row).
+//
+// On GB300 FP64 runs at 1/64 of the FP32 rate, so every stage is laid out
+// for lane parallelism: no stage runs a long dependent FP64 chain in a
+// single lane per matrix (the implicit-shift QR of the bidiagonal would).
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels_bd.h"
+
+namespace mctrg {
+
+namespace {
+constexpr int kBdThreads = 256;
+constexpr int kBisThreads = 256;
+constexpr int kInvitIters = 3;
+constexpr double kEps = 0x1.0p-52;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  return s;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s = fmax(s, red[w]);
+  return s;
+}
+
+// Biased exponent field of a double (0 for zero and subnormals).
+__device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// 1. Householder bidiagonalization, one CTA per matrix.
+//    Left step k: H = I - tau v v^T with v = (1, x_{k+1..}/(alpha - beta))
+//    zeroes column k below the diagonal (each thread owns columns: the dot
+//    v^T A[:, j] and the rank-1 update of that column).  Right step k: the
+//    same on row k right of the superdiagonal (each warp owns rows: the dot
+//    A[i, :] u and the update of that row).
+__global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_smem) {
+  extern __shared__ double sm[];
+  const int n = a.n;
+  const int mat = blockIdx.x;
+  double* A = use_smem ? sm : a.W + (size_t)mat * n * n;
+  double* vbuf = use_smem ? sm + (size_t)n * n : sm;   // [n] current reflector
+  double* red = vbuf + n;                              // [32]
+  double* bd = a.bd + (size_t)mat * 3 * n;
+  const double* Mm = a.M + (size_t)mat * n * n;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int e = tid; e < n * n; e += nt) A[e] = Mm[e];
+  for (int e = tid; e < 3 * n; e += nt) bd[e] = 0.0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    // ---- left reflector on column k
+    double s = 0.0;
+    for (int i = k + 1 + tid; i < n; i += nt) { const double v = A[(size_t)i * n + k]; s = fma(v, v, s); }
+    const double xn2 = block_sum(s, red);
+    const double alpha = A[(size_t)k * n + k];
+    double tau = 0.0, beta = alpha;
+    if (xn2 > 0.0) {
+      beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
+      tau = (beta - alpha) / beta;
+      const double scal = 1.0 / (alpha - beta);
+      for (int i = k + 1 + tid; i < n; i += nt) vbuf[i] = A[(size_t)i * n + k] * scal;
+    }
+    __syncthreads();
+    if (tau != 0.0) {
+      for (int j = k + 1 + tid; j < n; j += nt) {
+        double w = A[(size_t)k * n + j];
+        for (int i = k + 1; i < n; ++i) w = fma(vbuf[i], A[(size_t)i * n + j], w);
+        w *= tau;
+        A[(size_t)k * n + j] -= w;
+        for (int i = k + 1; i < n; ++i) A[(size_t)i * n + j] = fma(-vbuf[i], w, A[(size_t)i * n + j]);
+      }
+    }
+    if (tid == 0) bd[k] = beta;
+    __syncthreads();
+    if (k >= n - 1) break;
+    // ---- right reflector on row k, columns k+1..
+    s = 0.0;
+    for (int j = k + 2 + tid; j < n; j += nt) { const double v = A[(size_t)k * n + j]; s = fma(v, v, s); }
+    const double yn2 = block_sum(s, red);
+    const double ar = A[(size_t)k * n + k + 1];
+    double taur = 0.0, betar = ar;
+    if (yn2 > 0.0) {
+      betar = -copysign(sqrt(fma(ar, ar, yn2)), ar);
+      taur = (betar - ar) / betar;
+      const double scal = 1.0 / (ar - betar);
+      for (int j = k + 2 + tid; j < n; j += nt) {
+        const double u = A[(size_t)k * n + j] * scal;
+        vbuf[j] = u;
+        A[(size_t)k * n + j] = u;            // kept for the back-transformation
+      }
+    }
+    if (tid == 0) { vbuf[k + 1] = 1.0; bd[n + k] = betar; bd[2 * n + k] = taur; }
+    __syncthreads();
+    if (taur != 0.0) {
+      for (int i = k + 1 + warp; i < n; i += nw) {
+        double* row = A + (size_t)i * n;
+        double y = 0.0;
+        for (int j = k + 1 + lane; j < n; j += 32) y = fma(row[j], vbuf[j], y);
+        for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+        y *= taur;
+        for (int j = k + 1 + lane; j < n; j += 32) row[j] = fma(-y, vbuf[j], row[j]);
+      }
+    }
+    __syncthreads();
+  }
+  if (use_smem) {
+    double* Wm = a.W + (size_t)mat * n * n;
+    for (int e = tid; e < n * n; e += nt) Wm[e] = A[e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. Sturm count: #{s_i < x} for the bidiagonal whose Golub-Kahan tridiagonal
+//    has squared off-diagonals oo[0 .. 2n-2] (normalized so that |T| <= 1),
+//    x > 0.  Sign changes of P_0 .. P_2n count the eigenvalues of T below x:
+//    the n values -s_i and those s_i < x.
+__device__ __forceinline__ int sturm_count(const double* __restrict__ oo, int n, double x) {
+  double pp = 1.0, p = -x;
+  int neg = 1;
+  const int m = 2 * n;
+  for (int k = 2; k <= m; ++k) {
+    double q = fma(-x, p, -oo[k - 2] * pp);
+    long long qb = __double_as_longlong(q);
+    if ((qb << 1) == 0) {                 // a zero minor: a tiny pivot of the opposite sign
+      q = -p * 0x1.0p-60;
+      qb = __double_as_longlong(q);
+    }
+    neg += (int)((unsigned long long)(qb ^ __double_as_longlong(p)) >> 63);
+    pp = p;
+    p = q;
+    const int em = max(exp_field(p), exp_field(pp));
+    if (em < 1023 - 400) {                // rescale both by 2^(1023 - em), exactly
+      const double sc = __hiloint2double((2046 - em) << 20, 0);
+      p *= sc;
+      pp *= sc;
+    }
+  }
+  return neg - n;
+}
+
+__global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int n, int n_pad, double* sig,
+                                                            int* perm, int* nnz, double* lns1, double zero_rel) {
+  extern __shared__ double sm[];
+  double* oo = sm;                                   // [2n]
+  int* cnt = (int*)(oo + 2 * n);                     // [kBisThreads]
+  __shared__ double red[32];
+  __shared__ int s_zlo, s_nnz;
+  const int mat = blockIdx.x, tid = threadIdx.x;
+  const double* d = bd + (size_t)mat * 3 * n;
+  const double* e = d + n;
+  double* sg = sig + (size_t)mat * n_pad;
+  // G = max_k (|o_{k-1}| + |o_k|) >= |T| >= s_1 (Gershgorin), omax = max |o_k| <= s_1
+  double g = 0.0, om = 0.0;
+  for (int k = tid; k < 2 * n - 1; k += kBisThreads) {
+    const double ok = fabs((k & 1) ? e[k >> 1] : d[k >> 1]);
+    const double on = (k + 1 < 2 * n - 1) ? fabs(((k + 1) & 1) ? e[(k + 1) >> 1] : d[(k + 1) >> 1]) : 0.0;
+    g = fmax(g, ok + on);
+    om = fmax(om, ok);
+  }
+  if (n == 1) { g = fabs(d[0]); om = g; }
+  const double G = block_max(g, red);
+  const double omax = block_max(om, red);
+  if (!(G > 0.0)) {                                  // the zero matrix
+    for (int r = tid; r < n_pad; r += kBisThreads) { sg[r] = 0.0; perm[(size_t)mat * n_pad + r] = r; }
+    if (tid == 0) { nnz[mat] = 0; if (lns1) lns1[mat] = -INFINITY; }
+    return;
+  }
+  const double invG = 1.0 / G;
+  for (int k = tid; k < 2 * n - 1; k += kBisThreads) {
+    const double ok = ((k & 1) ? e[k >> 1] : d[k >> 1]) * invG;
+    oo[k] = ok * ok;
+  }
+  const double zr = zero_rel > 0.0 ? zero_rel : (double)n * kEps;
+  const double tlo = zr * omax * invG;               // <= the zero threshold zr s_1 / G
+  __syncthreads();
+  // coarse grid: cnt[t] = #{s < x_t}, x_t = (t + 1) / T, the last point above |T|
+  const double xt = (tid == kBisThreads - 1) ? 1.0 + 0x1.0p-20 : (double)(tid + 1) / kBisThreads;
+  cnt[tid] = sturm_count(oo, n, xt);
+  if (tid == 0) s_zlo = sturm_count(oo, n, tlo);
+  __syncthreads();
+  const int zlo = s_zlo;
+  for (int r = tid; r < n; r += kBisThreads) {
+    const int j = n - 1 - r;                         // ascending index of the r-th largest
+    if (j < zlo) { sg[r] = 0.0; continue; }          // below tlo: a zero
+    int t = 0;
+    while (t < kBisThreads - 1 && cnt[t] < j + 1) ++t;
+    double lo = t > 0 ? (double)t / kBisThreads : 0.0;
+    double hi = (t == kBisThreads - 1) ? 1.0 + 0x1.0p-20 : (double)(t + 1) / kBisThreads;
+    while (hi - lo > 0x1.0p-51) {
+      const double mid = 0.5 * (lo + hi);
+      if (sturm_count(oo, n, mid) >= j + 1) hi = mid; else lo = mid;
+    }
+    sg[r] = G * (0.5 * (lo + hi));
+  }
+  for (int r = n + tid; r < n_pad; r += kBisThreads) sg[r] = 0.0;
+  for (int r = tid; r < n_pad; r += kBisThreads) perm[(size_t)mat * n_pad + r] = r;
+  if (tid == 0) s_nnz = 0;
+  __syncthreads();
+  const double s1 = sg[0];
+  const double tau = zr * s1;
+  int c = 0;
+  for (int r = tid; r < n; r += kBisThreads) c += sg[r] > tau;
+  if (c) atomicAdd(&s_nnz, c);
+  __syncthreads();
+  if (tid == 0) {
+    nnz[mat] = s1 > 0.0 ? s_nnz : 0;
+    if (lns1) lns1[mat] = s1 > 0.0 ? log(s1) : -INFINITY;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. Inverse iteration, one warp per matrix (persistent over matrices), lane a
+//    for the a-th kept index.  Scratch per warp slot, interleaved by lane:
+//    DG, DU, DU2 (the LU factors of T - s I with partial pivoting, in the
+//    layout of LAPACK's dgtsv) and X (the iterate), 4 x 2n x 32 doubles.
+__global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a) {
+  const int lane = threadIdx.x;
+  const int n = a.n, m = 2 * n;
+  double* scr = a.scratch + (size_t)blockIdx.x * 4 * m * 32;
+#define DG(i) scr[((size_t)0 * m + (i)) * 32 + lane]
+#define DU(i) scr[((size_t)1 * m + (i)) * 32 + lane]
+#define DU2(i) scr[((size_t)2 * m + (i)) * 32 + lane]
+#define XB(i) scr[((size_t)3 * m + (i)) * 32 + lane]
+#define XL(l, i) scr[((size_t)3 * m + (i)) * 32 + (l)]
+  for (int s = blockIdx.x; s < a.S; s += gridDim.x) {
+    const int nk = a.nk[s];
+    const int* kept = a.kept + (size_t)s * 32;
+    const double* sg = a.sig + (size_t)s * a.n_pad;
+    const double* bd = a.bd + (size_t)s * 3 * n;
+    double* vout = a.vrows + (size_t)s * 32 * n;
+    // |T| (max |o_k|): T and s are scaled by 1/|T|, the pivot floor is eps
+    double tn = 0.0;
+    for (int i = lane; i < n; i += 32) tn = fmax(tn, fmax(fabs(bd[i]), fabs(bd[n + i])));
+    for (int o = 16; o > 0; o >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    const double its = tn > 0.0 ? 1.0 / tn : 0.0;
+    const bool on = lane < nk;
+    const double sgm = on ? sg[kept[lane]] * its : 0.0;
+    const double floor_piv = kEps;
+    if (on) {                                        // start vector, different per lane
+      for (int i = 0; i < m; ++i) XB(i) = 1.0 + 0.25 * (double)((i * (2 * lane + 3)) % 17) * (1.0 / 17.0);
+    }
+    for (int iter = 0; iter < kInvitIters; ++iter) {
+      if (on) {
+        // factor T - s I = P L U, applying L^-1 P^T to X on the fly
+        for (int i = 0; i < m; ++i) {
+          DG(i) = -sgm;
+          DU(i) = i < m - 1 ? ((i & 1) ? bd[n + (i >> 1)] : bd[i >> 1]) * its : 0.0;
+          DU2(i) = 0.0;
+        }
+        for (int i = 0; i < m - 1; ++i) {
+          const double dli = ((i & 1) ? bd[n + (i >> 1)] : bd[i >> 1]) * its;   // sub-diagonal = off-diagonal
+          const double dgi = DG(i);
+          if (fabs(dgi) >= fabs(dli)) {
+            const double gpiv = (dgi == 0.0) ? floor_piv : dgi;
+            DG(i) = gpiv;
+            const double f = dli / gpiv;
+            DG(i + 1) = DG(i + 1) - f * DU(i);
+            XB(i + 1) = XB(i + 1) - f * XB(i);
+          } else {
+            const double f = dgi / dli;
+            DG(i) = dli;
+            const double t = DG(i + 1);
+            DG(i + 1) = DU(i) - f * t;
+            DU(i) = t;
+            if (i < m - 2) {
+              const double du1 = DU(i + 1);
+              DU2(i) = du1;
+              DU(i + 1) = -f * du1;
+            }
+            const double xi = XB(i), xi1 = XB(i + 1);
+            XB(i) = xi1;
+            XB(i + 1) = xi - f * xi1;
+          }
+        }
+        if (DG(m - 1) == 0.0) DG(m - 1) = floor_piv;
+        // back substitution U x = y
+        XB(m - 1) = XB(m - 1) / DG(m - 1);
+        if (m > 1) XB(m - 2) = (XB(m - 2) - DU(m - 2) * XB(m - 1)) / DG(m - 2);
+        for (int i = m - 3; i >= 0; --i) {
+          XB(i) = (XB(i) - DU(i) * XB(i + 1) - DU2(i) * XB(i + 2)) / DG(i);
+          if (exp_field(XB(i)) > 1023 + 600) {        // growth through tiny pivots: rescale x[i..]
+            for (int q = i; q < m; ++q) XB(q) *= 0x1.0p-600;
+          }
+        }
+        double s2 = 0.0;
+        for (int i = 0; i < m; ++i) s2 = fma(XB(i), XB(i), s2);
+        const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+        for (int i = 0; i < m; ++i) XB(i) *= inv;
+      }
+      // Gram-Schmidt against the earlier kept vectors of the same cluster
+      // (a chain of kept values less than 1e-3 |T| apart), in lane order
+      for (int c = 1; c < nk; ++c) {
+        __syncwarp();
+        if (sg[kept[c - 1]] - sg[kept[c]] > 1e-3 * tn) continue;
+        if (lane == c) {
+          int p0 = c - 1;
+          while (p0 > 0 && sg[kept[p0 - 1]] - sg[kept[p0]] <= 1e-3 * tn) --p0;
+          // (the earlier cluster members' iterates are final for this iteration)
+          for (int p = p0; p < c; ++p) {
+            double dot = 0.0;
+            for (int i = 0; i < m; ++i) dot = fma(XL(p, i), XB(i), dot);
+            for (int i = 0; i < m; ++i) XB(i) = fma(-dot, XL(p, i), XB(i));
+          }
+          double s2 = 0.0;
+          for (int i = 0; i < m; ++i) s2 = fma(XB(i), XB(i), s2);
+          const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+          for (int i = 0; i < m; ++i) XB(i) *= inv;
+        }
+      }
+      __syncwarp();
+    }
+    if (on) {                                        // v_B = even entries, normalized
+      double s2 = 0.0;
+      for (int i = 0; i < n; ++i) s2 = fma(XB(2 * i), XB(2 * i), s2);
+      const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+      for (int i = 0; i < n; ++i) vout[(size_t)lane * n + i] = XB(2 * i) * inv;
+    }
+    __syncwarp();
+  }
+#undef DG
+#undef DU
+#undef DU2
+#undef XB
+#undef XL
+}
+
+// ---------------------------------------------------------------------------
+// 4. v = H_0 H_1 ... H_{n-3} v_B, one CTA per matrix, vectors in shared
+//    memory, 4 vectors per warp (warps independent: no block barrier inside
+//    the reflector loop).  The four dot products of a warp are reduced
+//    together: one exchange halves four values to two, a second to one, then
+//    three butterfly steps finish the sum.
+__global__ void k_bd_backtr(BdVecArgs a) {
+  extern __shared__ double V[];                      // [32][n]
+  const int n = a.n, s = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nk = a.nk[s];
+  double* vrow = a.vrows + (size_t)s * 32 * n;
+  for (int e = threadIdx.x; e < nk * n; e += blockDim.x) V[e] = vrow[e];
+  __syncthreads();
+  const double* R = a.R + (size_t)s * n * n;
+  const double* tauR = a.bd + (size_t)s * 3 * n + 2 * n;
+  const int a0 = warp * 4;
+  if (a0 < nk) {
+    double* V0 = V + (size_t)a0 * n;
+    const int na = min(4, nk - a0);
+    const bool hi16 = lane & 16, hi8 = lane & 8;
+    for (int k = n - 3; k >= 0; --k) {
+      const double taur = tauR[k];
+      if (taur == 0.0) continue;
+      const double* u = R + (size_t)k * n;           // u[k+1] = 1, u[k+2..n-1] stored
+      double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+      for (int j = k + 1 + lane; j < n; j += 32) {
+        const double uj = (j == k + 1) ? 1.0 : u[j];
+        p0 = fma(uj, V0[j], p0);
+        if (na > 1) p1 = fma(uj, V0[n + j], p1);
+        if (na > 2) p2 = fma(uj, V0[2 * n + j], p2);
+        if (na > 3) p3 = fma(uj, V0[3 * n + j], p3);
+      }
+      double q0 = hi16 ? p2 : p0, q1 = hi16 ? p3 : p1;
+      const double r0 = hi16 ? p0 : p2, r1 = hi16 ? p1 : p3;
+      q0 += __shfl_xor_sync(0xffffffffu, r0, 16);
+      q1 += __shfl_xor_sync(0xffffffffu, r1, 16);
+      double t = hi8 ? q1 : q0;
+      const double tr = hi8 ? q0 : q1;
+      t += __shfl_xor_sync(0xffffffffu, tr, 8);
+      t += __shfl_xor_sync(0xffffffffu, t, 4);
+      t += __shfl_xor_sync(0xffffffffu, t, 2);
+      t += __shfl_xor_sync(0xffffffffu, t, 1);
+      // lanes with bits (4, 3) = (h, l) now hold the dot of vector 2 h + l
+      const double w0 = taur * __shfl_sync(0xffffffffu, t, 0);
+      const double w1 = taur * __shfl_sync(0xffffffffu, t, 8);
+      const double w2 = taur * __shfl_sync(0xffffffffu, t, 16);
+      const double w3 = taur * __shfl_sync(0xffffffffu, t, 24);
+      for (int j = k + 1 + lane; j < n; j += 32) {
+        const double uj = (j == k + 1) ? 1.0 : u[j];
+        V0[j] = fma(-w0, uj, V0[j]);
+        if (na > 1) V0[n + j] = fma(-w1, uj, V0[n + j]);
+        if (na > 2) V0[2 * n + j] = fma(-w2, uj, V0[2 * n + j]);
+        if (na > 3) V0[3 * n + j] = fma(-w3, uj, V0[3 * n + j]);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  const int* kept = a.kept + (size_t)s * 32;
+  const double* sg = a.sig + (size_t)s * a.n_pad;
+  for (int e = threadIdx.x; e < nk * n; e += blockDim.x) vrow[e] = a.unit_rows ? V[e] : sg[kept[e / n]] * V[e];
+}
+
+// ---------------------------------------------------------------------------
+cudaError_t launch_bidiag(const BidiagArgs& a, cudaStream_t st) {
+  if (a.S <= 0) return cudaSuccess;
+  const int n = a.n;
+  const size_t rows = (size_t)n * n * sizeof(double), aux = (size_t)(n + 32) * sizeof(double);
+  const int use_smem = rows + aux <= 200 * 1024;
+  // rows in the global workspace: ask for enough shared memory that one CTA
+  // runs per SM, so the resident matrices stay in L2
+  const size_t smem = use_smem ? rows + aux : std::max<size_t>(aux, 120 * 1024);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_bidiag, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 1024);
+    attr = true;
+  }
+  k_bidiag<<<a.S, kBdThreads, smem, st>>>(a, use_smem);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bd_bisect(const double* bd, int n, int n_pad, int S, double* sig, int* perm, int* nnz,
+                             double* lns1, double zero_rel, cudaStream_t st) {
+  if (S <= 0) return cudaSuccess;
+  const size_t smem = (size_t)2 * n * sizeof(double) + kBisThreads * sizeof(int);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_bd_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_bd_bisect<<<S, kBisThreads, smem, st>>>(bd, n, n_pad, sig, perm, nnz, lns1, zero_rel);
+  return cudaGetLastError();
+}
+
+// Warp slots of the inverse iteration: enough to fill the GPU, few enough that
+// their scratch (4 x 2n x 32 doubles each) stays near the size of L2.
+static int invit_slots(int n, int S) {
+  const size_t per = (size_t)4 * 2 * n * 32 * sizeof(double);
+  const int by_l2 = (int)std::max<size_t>(152, (size_t)96 * 1024 * 1024 / per);
+  return std::max(1, std::min(S, std::min(by_l2, 152 * 8)));
+}
+
+size_t bd_vectors_scratch_doubles(int n, int S) { return (size_t)invit_slots(n, S) * 4 * 2 * n * 32; }
+
+cudaError_t launch_bd_vectors(const BdVecArgs& a, cudaStream_t st) {
+  if (a.S <= 0) return cudaSuccess;
+  const size_t smem = (size_t)32 * a.n * sizeof(double);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  k_bd_invit<<<invit_slots(a.n, a.S), 32, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_bd_backtr, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_bd_backtr<<<a.S, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mctrg

@@ -72,6 +72,11 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
     const int nz = (s1 > 0.0) ? a.nnz[slot] : 0;
     const bool sample = a.stochastic && nz > chi;
 
+    if (a.mode == 2) {                         // choices made earlier (split form)
+      if (tid < 32) { s_kept[tid] = a.kept[it * 32 + tid]; s_sigt[tid] = a.sigt[it * 32 + tid]; }
+      if (tid == 0) { s_nk = a.nk[it]; s_flags = 0; }
+      __syncthreads();
+    } else {
     for (int i = tid; i < np; i += kThreads) {
       const double v = (i < nz) ? sg[i] / s1 : 0.0;
       wn[i] = v;
@@ -171,14 +176,29 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
     }
     __syncthreads();
 
-    const int nk = s_nk;
+    const int nk0 = s_nk;
     if (sample) {                              // near-tie flags
       uint32_t fl = 0;
       for (int i = tid; i + 1 < nz; i += kThreads)
         if (inset[i] != inset[i + 1] && (wn[i] - wn[i + 1]) <= GAP_TOL) fl |= FLAG_SPLIT_CLUSTER;
-      if (tid < nk && wn[s_kept[tid]] < TINY_TOL) fl |= FLAG_TINY_KEPT;
+      if (tid < nk0 && wn[s_kept[tid]] < TINY_TOL) fl |= FLAG_TINY_KEPT;
       if (fl) atomicOr(&s_flags, fl);
     }
+    if (a.mode == 1) {                         // split form: hand the choices on
+      __syncthreads();
+      if (tid < 32) {
+        a.kept[it * 32 + tid] = tid < nk0 ? s_kept[tid] : 0;
+        a.sigt[it * 32 + tid] = tid < nk0 ? s_sigt[tid] : 0.0;
+      }
+      if (tid == 0) {
+        a.nk[it] = nk0;
+        if (a.iflags && s_flags) a.iflags[item - a.h_item0] |= s_flags;
+      }
+      __syncthreads();
+      continue;
+    }
+    }
+    const int nk = s_nk;
 
     // ---- halves ----
     double* Hl = a.H + (size_t)(item - a.h_item0) * 2 * n * kc;
@@ -190,7 +210,8 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
       double v = 0.0;
       if (al < nk) {
         const int r = s_kept[al];
-        v = sqrt(s_sigt[al]) * Wm[(size_t)pm[r] * n + col] / sg[r];
+        const double* brow = a.mode == 2 ? a.vrows + ((size_t)it * 32 + al) * n : Wm + (size_t)pm[r] * n;
+        v = sqrt(s_sigt[al]) * brow[col] / sg[r];
       }
       Hr[idx] = v;
     }
@@ -213,7 +234,8 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
         __syncthreads();
         for (int idx = tid; idx < nv * n; idx += kThreads) {
           const int q = idx / n, col = idx - q * n;
-          vbuf[idx] = Wm[(size_t)pm[s_kept[a0 + q]] * n + col];
+          vbuf[idx] = a.mode == 2 ? a.vrows[((size_t)it * 32 + a0 + q) * n + col]
+                                  : Wm[(size_t)pm[s_kept[a0 + q]] * n + col];
         }
         __syncthreads();
         for (int row = warp; row < n; row += kThreads / 32) {
@@ -242,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
       }
     }
     __syncthreads();
-    if (tid == 0 && a.iflags && s_flags) a.iflags[item - a.h_item0] |= s_flags;
+    if (tid == 0 && a.iflags && s_flags && a.mode == 0) a.iflags[item - a.h_item0] |= s_flags;
     __syncthreads();
   }
 }

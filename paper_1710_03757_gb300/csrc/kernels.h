@@ -51,6 +51,16 @@ struct SampleArgs {
   int64_t h_item0;      // item index of H[0] (items below it are not stored)
   uint32_t* iflags;     // [items] |= truncation flags (indexed item - h_item0); may be null
   double* scratch;      // tables: gridDim * (n + 1) * (2 chi + 1) doubles
+  // Split form (bidiagonalization route, whose vectors exist only for the kept
+  // indices): mode 1 chooses and writes kept[it][32] (ranks, ascending),
+  // sigt[it][32] (reweighted values s~) and nk[it], without halves; mode 2
+  // reads them back and writes the halves from vrows[it][a][col] = s_r v_r[col]
+  // (r = kept[it][a]) instead of W / perm.  it = item - item0.  mode 0: both.
+  int mode;
+  int* kept;
+  double* sigt;
+  int* nk;
+  const double* vrows;
 };
 cudaError_t launch_sample_split(const SampleArgs& a, cudaStream_t st, int grid);
 size_t sample_scratch_doubles(int n, int chi, int grid);

@@ -18,6 +18,7 @@
 #include "../../include/mctrg.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "kernels_bd.h"
 #include "kernels_tc.h"
 #include "mctrg_internal.h"
 
@@ -77,6 +78,7 @@ extern "C" int mctrg_options_default(mctrg_options* opt) {
 extern "C" int mctrg_create(const mctrg_options* opt, mctrg_ctx_t* out) {
   if (!opt || !out) return MCTRG_EINVAL;
   if (opt->precision < MCTRG_FP64 || opt->precision > MCTRG_BF16X3) return MCTRG_EINVAL;
+  if (opt->svd < MCTRG_SVD_AUTO || opt->svd > MCTRG_SVD_BIDIAG) return MCTRG_EINVAL;
   *out = nullptr;
   int ndev = 0;
   CK(cudaGetDeviceCount(&ndev));
@@ -163,7 +165,7 @@ void mctrg_ctx::release_all() {
   DevBuf* all[] = {&T0, &shM, &shW, &shSig, &shPerm, &shNnz, &shLns1, &shU, &shH, &Hbuf[0], &Hbuf[1],
                    &Mb, &Wb, &Xb, &Yb, &sigb, &permb, &nnzb, &ilns1, &iflags, &lnacc, &tflags,
                    &scratch, &o_lnabs, &o_sign, &o_flags, &o_tflags, &stats, &tcXh, &tcYh, &tcXl,
-                   &tcYl, &tcScale, &tcErr};
+                   &tcYl, &tcScale, &tcErr, &bdb, &keptb, &sigtb, &nkb, &vrowsb, &bdscr};
   for (DevBuf* b : all) b->release();
 }
 
@@ -268,6 +270,13 @@ int mctrg_ctx::init_from_device_tensor(int D0, int L_, int chi_) {
   return MCTRG_OK;
 }
 
+// SVD route of a level whose n x n matrices are X Yt^T with inner dimension K.
+bool mctrg_ctx::use_bidiag(int n, int K) const {
+  if (opt.svd == MCTRG_SVD_JACOBI) return false;
+  if (opt.svd == MCTRG_SVD_BIDIAG) return n >= 2;
+  return n >= 64 && 2 * K >= n;
+}
+
 static bool is_pow2(int L) { return L >= 2 && (L & (L - 1)) == 0; }
 
 extern "C" int mctrg_init_lattice(mctrg_ctx_t c, double beta, double h, int L, int chi) {
@@ -295,7 +304,7 @@ extern "C" int mctrg_init_tensor(mctrg_ctx_t c, const double* T0, int D, int L, 
 // Memory plan: bytes per trajectory of a chunk, and bytes per in-flight item.
 void mctrg_ctx::plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& total) const {
   size_t per_traj = 2 * sizeof(double) + sizeof(uint32_t);   // lnacc, tflags
-  size_t max_pair = 0, max_items = 0, per_item = 0;
+  size_t max_pair = 0, max_items = 0, per_item = 0, bd_scr = 0;
   for (int k = s0; k < nlev; ++k) {
     const LevelInfo& a = lv[k];
     size_t hk = (size_t)a.N * 2 * a.n * a.kc * sizeof(double);
@@ -306,6 +315,10 @@ void mctrg_ctx::plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& t
       const size_t d2 = (size_t)lv[k - 1].D * lv[k - 1].D;
       size_t pi = (2 * (size_t)a.n * d2 + (size_t)a.n * a.n + (size_t)a.n_pad * a.n + a.n_pad) * sizeof(double) +
                   (a.n_pad + 1) * sizeof(int) + sizeof(double) + sizeof(uint32_t);
+      if (use_bidiag(a.n, (int)d2)) {   // d, e, tau; kept values and vectors
+        pi += (3 * (size_t)a.n + 32 + 32 * (size_t)a.n) * sizeof(double) + 33 * sizeof(int);
+        bd_scr = std::max(bd_scr, bd_vectors_scratch_doubles(a.n, 1 << 16) * sizeof(double));
+      }
       per_item = std::max(per_item, pi);
     }
   }
@@ -318,7 +331,8 @@ void mctrg_ctx::plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& t
   const size_t budget = opt.hbm_budget_bytes;
   const size_t work_budget = std::max<size_t>(budget / 4, 1);
   S = per_item ? (int64_t)std::max<size_t>(1, std::min<size_t>(work_budget / per_item, 1 << 16)) : 1;
-  const size_t work = per_item * (size_t)S + sample_scratch_doubles(lv[nlev - 1].n, chi, 1024) * sizeof(double);
+  const size_t work = per_item * (size_t)S + sample_scratch_doubles(lv[nlev - 1].n, chi, 1024) * sizeof(double) +
+                      bd_scr;
   const size_t rest = budget > work ? budget - work : 0;
   B = (int64_t)(rest / std::max<size_t>(per_traj, 1));
   if (opt.max_chunk > 0) B = std::min<int64_t>(B, opt.max_chunk);
@@ -428,6 +442,24 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
     CK(permb.ensure(sizeof(int) * std::max<size_t>(max_np, 1)));
     CK(nnzb.ensure(sizeof(int) * std::max<int64_t>(S, 1)));
     CK(scratch.ensure(sizeof(double) * max_scr));
+    {  // bidiagonalization route buffers (levels that take it)
+      size_t bd_n = 0, bd_scr = 0;
+      for (int k = s0 + 1; k < nlev; ++k) {
+        const LevelInfo& a = lv[k];
+        if (!use_bidiag(a.n, lv[k - 1].D * lv[k - 1].D)) continue;
+        bd_n = std::max(bd_n, (size_t)a.n);
+        bd_scr = std::max(bd_scr, bd_vectors_scratch_doubles(a.n, (int)std::min<int64_t>(S, 1 << 16)));
+      }
+      if (bd_n) {
+        const size_t Ss = (size_t)std::max<int64_t>(S, 1);
+        CK(bdb.ensure(sizeof(double) * Ss * 3 * bd_n));
+        CK(keptb.ensure(sizeof(int) * Ss * 32));
+        CK(sigtb.ensure(sizeof(double) * Ss * 32));
+        CK(nkb.ensure(sizeof(int) * Ss));
+        CK(vrowsb.ensure(sizeof(double) * Ss * 32 * bd_n));
+        CK(bdscr.ensure(sizeof(double) * bd_scr));
+      }
+    }
     // tensor-core operands (mixed precision): per item X and Yt rounded, with scales
     const int prec = opt.precision;
     const int tc_kind = (prec == MCTRG_TF32 || prec == MCTRG_TF32X3) ? 0 : 1;
@@ -512,28 +544,53 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
             CK(timed(MCTRG_K_GEMM, Si, Si * 2.0 * a.n * a.n * gm.K, 8.0 * Si * (2.0 * a.n * gm.K + (double)a.n * a.n),
                      [&] { return launch_gemm_f64(gm, st); }));
           }
-          JacobiArgs ja{};
-          ja.M = Mb.as<double>(); ja.W = Wb.as<double>(); ja.sig = sigb.as<double>();
-          ja.perm = permb.as<int>(); ja.lns1 = ilns1.as<double>() + i0; ja.nnz = nnzb.as<int>();
-          ja.mflags = iflags.as<uint32_t>() + i0; ja.n = a.n; ja.n_pad = a.n_pad; ja.S = (int)Si;
-          ja.max_sweeps = opt.max_sweeps;
-          if (used_tc) {
-            const double u = tc_unit_roundoff(prec);
-            ja.noise_u = u;
-            ja.zero_rel = std::min(std::sqrt((double)a.n) * u, 1.0 / 64.0);
-          }
           const double nn = a.n;
-          CK(timed(MCTRG_K_JACOBI, Si, Si * ((8.0 / 3.0) * nn * nn * nn + 4.0 * nn * nn * a.kc),
-                   8.0 * Si * (nn * nn + (double)a.n_pad * nn + 1.5 * a.n_pad), [&] { return launch_jacobi(ja, st); }));
+          const double zero_rel = used_tc ? std::min(std::sqrt(nn) * tc_unit_roundoff(prec), 1.0 / 64.0) : 0.0;
           SampleArgs sa{};
-          sa.M = Mb.as<double>(); sa.W = Wb.as<double>(); sa.sig = sigb.as<double>();
-          sa.perm = permb.as<int>(); sa.nnz = nnzb.as<int>(); sa.Urows = nullptr;
+          sa.M = Mb.as<double>(); sa.sig = sigb.as<double>(); sa.nnz = nnzb.as<int>(); sa.Urows = nullptr;
           sa.n = a.n; sa.n_pad = a.n_pad; sa.chi = chi; sa.kc = a.kc; sa.stochastic = 1; sa.shared_svd = 0;
           sa.item0 = i0; sa.n_items = Si; sa.N = a.N; sa.L = L; sa.level = k; sa.seed = seed;
           sa.traj0 = traj0; sa.H = Hbuf[cur].as<double>(); sa.h_item0 = 0;
           sa.iflags = iflags.as<uint32_t>(); sa.scratch = scratch.as<double>();
-          CK(timed(MCTRG_K_SAMPLE, Si, Si * (4.0 * nn * a.kc + 2.0 * nn * nn * a.kc),
-                   8.0 * Si * (2.0 * nn * nn + 2.0 * nn * a.kc), [&] { return launch_sample_split(sa, st, grid_s); }));
+          if (use_bidiag(a.n, Kd)) {
+            // bidiagonalization, bisection, choice of the kept indices, their vectors, halves
+            BidiagArgs ba{};
+            ba.M = Mb.as<double>(); ba.W = Wb.as<double>(); ba.bd = bdb.as<double>(); ba.n = a.n; ba.S = (int)Si;
+            CK(timed(MCTRG_K_BIDIAG, Si, Si * (8.0 / 3.0) * nn * nn * nn, 8.0 * Si * (2.0 * nn * nn + 3.0 * nn),
+                     [&] { return launch_bidiag(ba, st); }));
+            CK(timed(MCTRG_K_BISECT, Si, 0.0, 8.0 * Si * (3.0 * nn + a.n_pad) + 4.0 * Si * (a.n_pad + 1), [&] {
+              return launch_bd_bisect(bdb.as<double>(), a.n, a.n_pad, (int)Si, sigb.as<double>(), permb.as<int>(),
+                                      nnzb.as<int>(), ilns1.as<double>() + i0, zero_rel, st); }));
+            sa.mode = 1; sa.kept = keptb.as<int>(); sa.sigt = sigtb.as<double>(); sa.nk = nkb.as<int>();
+            sa.W = nullptr; sa.perm = permb.as<int>();
+            CK(timed(MCTRG_K_SAMPLE, Si, Si * 4.0 * nn * a.kc, 8.0 * Si * (a.n_pad + 2.0 * 32),
+                     [&] { return launch_sample_split(sa, st, grid_s); }));
+            BdVecArgs va{};
+            va.bd = bdb.as<double>(); va.R = Wb.as<double>(); va.sig = sigb.as<double>(); va.kept = keptb.as<int>();
+            va.nk = nkb.as<int>(); va.vrows = vrowsb.as<double>(); va.scratch = bdscr.as<double>();
+            va.n = a.n; va.n_pad = a.n_pad; va.S = (int)Si;
+            CK(timed(MCTRG_K_VECTORS, Si, Si * (2.0 * nn * nn * a.kc + 40.0 * nn * a.kc),
+                     8.0 * Si * (nn * nn / 2.0 + 3.0 * nn + 2.0 * 32 * nn), [&] { return launch_bd_vectors(va, st); }));
+            sa.mode = 2; sa.vrows = vrowsb.as<double>();
+            CK(timed(MCTRG_K_SAMPLE, Si, Si * 2.0 * nn * nn * a.kc, 8.0 * Si * (2.0 * nn * nn + 2.0 * nn * a.kc),
+                     [&] { return launch_sample_split(sa, st, grid_s); }));
+          } else {
+            JacobiArgs ja{};
+            ja.M = Mb.as<double>(); ja.W = Wb.as<double>(); ja.sig = sigb.as<double>();
+            ja.perm = permb.as<int>(); ja.lns1 = ilns1.as<double>() + i0; ja.nnz = nnzb.as<int>();
+            ja.mflags = iflags.as<uint32_t>() + i0; ja.n = a.n; ja.n_pad = a.n_pad; ja.S = (int)Si;
+            ja.max_sweeps = opt.max_sweeps;
+            if (used_tc) {
+              ja.noise_u = tc_unit_roundoff(prec);
+              ja.zero_rel = zero_rel;
+            }
+            CK(timed(MCTRG_K_JACOBI, Si, Si * ((8.0 / 3.0) * nn * nn * nn + 4.0 * nn * nn * a.kc),
+                     8.0 * Si * (nn * nn + (double)a.n_pad * nn + 1.5 * a.n_pad), [&] { return launch_jacobi(ja, st); }));
+            sa.mode = 0; sa.W = Wb.as<double>(); sa.perm = permb.as<int>();
+            CK(timed(MCTRG_K_SAMPLE, Si, Si * (4.0 * nn * a.kc + 2.0 * nn * nn * a.kc),
+                     8.0 * Si * (2.0 * nn * nn + 2.0 * nn * a.kc), [&] { return launch_sample_split(sa, st, grid_s); }));
+        
+          }
         }
         CK(timed(MCTRG_K_OTHER, Bc, 0.0, 12.0 * items, [&] {
           return launch_traj_accum(ilns1.as<double>(), iflags.as<uint32_t>(), a.N, Bc, lnacc.as<double>(),

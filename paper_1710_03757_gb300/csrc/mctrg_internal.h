@@ -48,6 +48,7 @@ struct mctrg_ctx {
   mctrg::DevBuf Hbuf[2], Mb, Wb, Xb, Yb, sigb, permb, nnzb, ilns1, iflags, lnacc, tflags, scratch;
   mctrg::DevBuf o_lnabs, o_sign, o_flags, o_tflags, stats;
   mctrg::DevBuf tcXh, tcYh, tcXl, tcYl, tcScale, tcErr;   // tensor-core operands
+  mctrg::DevBuf bdb, keptb, sigtb, nkb, vrowsb, bdscr;    // bidiagonalization route
 
   // per-kernel-class statistics (MCTRG_K_*)
   mctrg_kernel_stat kstat[MCTRG_K_COUNT]{};
@@ -80,6 +81,7 @@ struct mctrg_ctx {
   void resolve_events();   // after a stream synchronize
 
   int init_from_device_tensor(int D0, int L, int chi);
+  bool use_bidiag(int n, int K) const;
   void plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& total) const;
   int run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs, int8_t* sign, uint8_t* flags,
           mctrg_estimate* est);

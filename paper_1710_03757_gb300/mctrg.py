@@ -23,9 +23,11 @@ EXPORTS = [
     "mctrg_server_create", "mctrg_server_submit", "mctrg_server_poll", "mctrg_server_wait",
     "mctrg_server_destroy", "mctrg_plan_level", "mctrg_philox_uniform", "mctrg_kernel_stats",
     "mctrg_reset_kernel_stats", "mctrg_svd_batched", "mctrg_svd_batched_noalloc",
+    "mctrg_svd_bidiag_batched",
 ]
-K_FORM_XY, K_GEMM, K_JACOBI, K_SAMPLE, K_TRACE, K_OTHER, K_COUNT = range(7)
-KERNEL_NAMES = ["form_xy", "gemm", "jacobi", "sample_split", "trace", "other"]
+K_FORM_XY, K_GEMM, K_JACOBI, K_SAMPLE, K_TRACE, K_OTHER, K_BIDIAG, K_BISECT, K_VECTORS, K_COUNT = range(10)
+KERNEL_NAMES = ["form_xy", "gemm", "jacobi", "sample_split", "trace", "other", "bidiag", "bisect", "vectors"]
+SVD_AUTO, SVD_JACOBI, SVD_BIDIAG = 0, 1, 2
 
 
 class KernelStat(ctypes.Structure):
@@ -36,7 +38,7 @@ class KernelStat(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("max_sweeps", ctypes.c_int),
-                ("max_chunk", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("max_chunk", ctypes.c_int), ("profile", ctypes.c_int), ("svd", ctypes.c_int)]
 
 
 class Estimate(ctypes.Structure):
@@ -86,6 +88,7 @@ def lib():
             "mctrg_reset_kernel_stats": (c_int, [vp]),
             "mctrg_svd_batched": (c_int, [vp, c_int, i64, vp, vp, c_int, vp]),
             "mctrg_svd_batched_noalloc": (c_int, [vp, c_int, i64, vp, vp, c_int, vp]),
+            "mctrg_svd_bidiag_batched": (c_int, [vp, c_int, i64, vp, c_int, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -132,9 +135,9 @@ def mctrg_options_default():
 
 
 def make_options(device=0, stream=None, precision=MCTRG_FP64, hbm_budget_bytes=0, max_sweeps=0,
-                 max_chunk=0, profile=0):
+                 max_chunk=0, profile=0, svd=SVD_AUTO):
     o = mctrg_options_default()
-    o.device, o.precision, o.profile = int(device), int(precision), int(profile)
+    o.device, o.precision, o.profile, o.svd = int(device), int(precision), int(profile), int(svd)
     o.cuda_stream = stream
     o.hbm_budget_bytes, o.max_sweeps, o.max_chunk = int(hbm_budget_bytes), int(max_sweeps), int(max_chunk)
     return o
@@ -201,6 +204,15 @@ def mctrg_svd_batched_noalloc(M, sigma, vt=None, max_sweeps=0, stream=None):
     device allocations (for callers that cannot allocate)."""
     batch, n = int(M.shape[0]), int(M.shape[-1])
     return lib().mctrg_svd_batched_noalloc(_ptr(M), n, batch, _ptr(sigma), _ptr(vt), int(max_sweeps), stream)
+
+
+def mctrg_svd_bidiag_batched(M, sigma, vt=None, stream=None):
+    """Bidiagonalization route: M (batch, n, n) float64 device tensor; sigma
+    (batch, n); vt (batch, n_vec, n) receives the unit right vectors of the
+    n_vec largest singular values (None: values only)."""
+    batch, n = int(M.shape[0]), int(M.shape[-1])
+    nv = 0 if vt is None else int(vt.shape[1])
+    return lib().mctrg_svd_bidiag_batched(_ptr(M), n, batch, _ptr(sigma), nv, _ptr(vt), stream)
 
 
 def mctrg_destroy(ctx):

@@ -1,0 +1,151 @@
+"""The bidiagonalization route of the batched SVD (K2): Householder reduction,
+bisection on Sturm counts of the Golub-Kahan tridiagonal, inverse iteration
+and back-transformation of the kept vectors.
+
+Kernel level against LAPACK (singular values to a few eps |M| absolute, right
+vectors by residual, orthonormality and, where the value is isolated, by angle),
+then the whole hot path with the route forced on every level against the
+oracle, per trajectory, at the parity tolerance of the Jacobi route.
+"""
+import numpy as np
+import pytest
+
+from oracle import ising
+from oracle.trg import Problem, run_many
+from paper_1710_03757_gb300 import build, mctrg
+from paper_1710_03757_gb300.workloads import generic_tensor, seed_for
+
+from test_gpu_parity import compare, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    build.build()
+    mctrg.lib()
+    return pytest.importorskip("torch")
+
+
+def _matrices(n, batch, kind, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(batch):
+        if kind == "gauss":
+            A = rng.standard_normal((n, n))
+        elif kind == "graded":           # singular values over 14 decades
+            U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+            V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+            A = (U * np.logspace(0, -14, n)) @ V.T
+        elif kind == "pairs":            # every singular value twice
+            U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+            V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+            s = np.repeat(np.linspace(1.0, 0.05, (n + 1) // 2), 2)[:n]
+            A = (U * s) @ V.T
+        else:                            # rank n // 3
+            r = max(1, n // 3)
+            A = rng.standard_normal((n, r)) @ rng.standard_normal((r, n))
+        out.append(A)
+    return np.stack(out)
+
+
+def _run(torch, A, nv):
+    batch, n = A.shape[0], A.shape[1]
+    M = torch.tensor(A, device="cuda")
+    sig = torch.zeros((batch, n), dtype=torch.float64, device="cuda")
+    vt = torch.zeros((batch, nv, n), dtype=torch.float64, device="cuda") if nv else None
+    st = mctrg.mctrg_svd_bidiag_batched(M, sig, vt)
+    assert st == 0, mctrg.mctrg_strerror(st)
+    torch.cuda.synchronize()
+    return sig.cpu().numpy(), (vt.cpu().numpy() if nv else None)
+
+
+@pytest.mark.parametrize("n", [2, 3, 16, 33, 64, 100, 256])
+@pytest.mark.parametrize("kind", ["gauss", "graded", "lowrank", "pairs"])
+def test_values_and_kept_vectors_against_lapack(torch, n, kind):
+    batch = 5 if n >= 256 else 12
+    nv = min(16, n)
+    A = _matrices(n, batch, kind, seed=1000 + n * 7 + len(kind))
+    sg, V = _run(torch, A, nv)
+    for b in range(batch):
+        _, ref, Vr = np.linalg.svd(A[b])
+        s1 = ref[0]
+        np.testing.assert_allclose(sg[b], ref, atol=1e-13 * s1 * max(1, n) ** 0.5, rtol=0)
+        Vb = V[b]
+        np.testing.assert_allclose(Vb @ Vb.T, np.eye(nv), atol=1e-12)
+        # residual of the normal equations, A^T A v = s^2 v, relative to s_1^2
+        R = A[b].T @ (A[b] @ Vb.T) - Vb.T * sg[b][:nv] ** 2
+        assert np.abs(R).max() <= 1e-12 * s1 * s1
+        for r in range(nv):
+            gap = min([abs(ref[r] - ref[q]) for q in (r - 1, r + 1) if 0 <= q < n] + [np.inf])
+            if gap > 1e-3 * s1 and ref[r] > 1e-6 * s1:
+                # isolated value: the vector itself, to about eps |A| / gap
+                err = min(np.linalg.norm(Vb[r] - Vr[r]), np.linalg.norm(Vb[r] + Vr[r]))
+                assert err <= 1e-12 + 1e-13 * s1 / gap
+            else:
+                # cluster: the vector lies in the span of the cluster's vectors
+                C = [q for q in range(n) if abs(ref[q] - ref[r]) <= 2e-3 * s1]
+                proj = Vr[C] @ Vb[r]
+                assert abs(np.linalg.norm(proj) - 1.0) <= 1e-10
+
+
+def test_zero_and_tiny_matrices(torch):
+    A = np.zeros((3, 8, 8))
+    A[1, 0, 0] = 1e-300                  # far below the underflow guard's range
+    A[2] = np.diag(np.arange(8.0, 0.0, -1.0))
+    sg, V = _run(torch, A, 4)
+    assert np.all(sg[0] == 0.0)
+    assert sg[1][0] == pytest.approx(1e-300, rel=1e-12) and np.all(sg[1][1:] == 0.0)
+    np.testing.assert_allclose(sg[2], np.arange(8.0, 0.0, -1.0), rtol=0, atol=1e-14 * 8)
+    np.testing.assert_allclose(np.abs(V[2]), np.eye(8)[:4], atol=1e-12)
+
+
+def test_errors():
+    build.build()
+    assert mctrg.lib().mctrg_svd_bidiag_batched(None, 8, 1, None, 0, None, None) == mctrg.MCTRG_EINVAL
+
+
+# ---- the whole path with the route forced ----------------------------------
+
+@pytest.mark.parametrize("L,chi,D,n", [(4, 2, 2, 300), (4, 3, 2, 300), (8, 4, 2, 120), (4, 4, 3, 80),
+                                       (8, 3, 3, 40)])
+def test_generic_tensor_parity_bidiag(torch, L, chi, D, n):
+    T0 = generic_tensor(D, seed=100 + 10 * L + chi + D)
+    seed = 0xC0FFEE + L + chi
+    gpu = gpu_run(L, chi, n, seed, T0=T0, svd=mctrg.SVD_BIDIAG)
+    orc = run_many(Problem(T0, L, chi), seed, 0, n)
+    assert compare(gpu, orc, min_ok=0.9) >= 0.9 * n
+
+
+@pytest.mark.parametrize("beta,h,L,chi,n", [(0.3, 0.1, 8, 4, 100), (0.44, 0.05, 8, 2, 200)])
+def test_ising_parity_bidiag(torch, beta, h, L, chi, n):
+    seed = 991 + L
+    gpu = gpu_run(L, chi, n, seed, beta=beta, h=h, svd=mctrg.SVD_BIDIAG)
+    orc = run_many(Problem(ising.site_tensor(beta, h), L, chi), seed, 0, n)
+    compare(gpu, orc, min_ok=0.5)
+
+
+def test_n64_parity_bidiag(torch):
+    T0 = generic_tensor(2, seed=7)
+    gpu = gpu_run(8, 8, 24, 5, T0=T0, svd=mctrg.SVD_BIDIAG)
+    orc = run_many(Problem(T0, 8, 8), 5, 0, 24, workers=4)
+    compare(gpu, orc, min_ok=0.8)
+
+
+@pytest.mark.parametrize("L,beta,h,n", [(16, 0.44, 0.0, 32), (32, 0.40, 0.05, 16)])
+def test_ising_chi16_parity_auto_route(torch, L, beta, h, n):
+    # the automatic route: bidiagonalization on the full-rank 256 x 256 levels
+    seed = seed_for(2) + L
+    gpu = gpu_run(L, 16, n, seed, beta=beta, h=h)
+    orc = run_many(Problem(ising.site_tensor(beta, h), L, 16), seed, 0, n, workers=8)
+    compare(gpu, orc, min_ok=0.5)
+
+
+def test_routes_agree_at_L1024(torch):
+    # the headline lattice: one trajectory through each route
+    a = gpu_run(1024, 16, 1, seed_for(2), beta=0.44, first=1, svd=mctrg.SVD_JACOBI)
+    b = gpu_run(1024, 16, 1, seed_for(2), beta=0.44, first=1)
+    assert a[2][0] == b[2][0] == 1
+    assert abs(a[1][0] - b[1][0]) <= 1e-10 * abs(a[1][0])
+    f = ising.onsager_minus_beta_f(0.44)
+    assert abs(b[1][0] / 1024 ** 2 - f) < 2e-3
