@@ -93,7 +93,8 @@ typedef struct {
  *           of the kept indices only (inverse iteration, back-transformation);
  *           (8/3) n^3 + O(n^2) flops whatever the rank.
  *   AUTO    BIDIAG where the matrices can have full rank (n >= 64 and the
- *           plaquette's inner dimension d^2 >= n / 2), JACOBI elsewhere. */
+ *           plaquette's inner dimension d^2 >= n / 2), JACOBI elsewhere.
+ * BIDIAG covers n <= 768 (chi <= 27); larger levels take JACOBI. */
 typedef enum { MCTRG_SVD_AUTO = 0, MCTRG_SVD_JACOBI = 1, MCTRG_SVD_BIDIAG = 2 } mctrg_svd_route;
 
 /* Estimate of Z from n trajectories (Sec. III Eq. infiniteEnsemble, Sec. V Eq.
