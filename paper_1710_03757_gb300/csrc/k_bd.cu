@@ -357,6 +357,27 @@ __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a) {
       const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
       for (int i = 0; i < n; ++i) vout[(size_t)lane * n + i] = XB(2 * i) * inv;
     }
+    // orthogonal z's of a cluster need not have orthogonal halves (values near
+    // the noise level mix +s and -s): orthonormalize the v's of each cluster too
+    for (int c = 1; c < nk; ++c) {
+      __syncwarp();
+      if (sg[kept[c - 1]] - sg[kept[c]] > 1e-3 * tn) continue;
+      if (lane == c) {
+        int p0 = c - 1;
+        while (p0 > 0 && sg[kept[p0 - 1]] - sg[kept[p0]] <= 1e-3 * tn) --p0;
+        double* vc = vout + (size_t)c * n;
+        for (int p = p0; p < c; ++p) {
+          const double* vp = vout + (size_t)p * n;
+          double dot = 0.0;
+          for (int i = 0; i < n; ++i) dot = fma(vp[i], vc[i], dot);
+          for (int i = 0; i < n; ++i) vc[i] = fma(-dot, vp[i], vc[i]);
+        }
+        double s2 = 0.0;
+        for (int i = 0; i < n; ++i) s2 = fma(vc[i], vc[i], s2);
+        const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+        for (int i = 0; i < n; ++i) vc[i] *= inv;
+      }
+    }
     __syncwarp();
   }
 #undef DG
