@@ -244,7 +244,9 @@ int mctrg_svd_batched_noalloc(const double* M, int n, int64_t batch, double* sig
  * vt (device, batch*n_vec*n; NULL when n_vec = 0) receives unit right vectors
  * as rows.  Each value carries an absolute error of a few 2^-52 |M|; vectors
  * of values closer than 1e-3 |M| to another are an orthonormal basis of their
- * cluster's subspace.  Allocates and frees its working memory.
+ * cluster's subspace; vectors of values at the noise level (a few 2^-52 n |M|
+ * and below: the numerical null space) are not determined and carry no
+ * guarantee.  Allocates and frees its working memory.
  * 2 <= n <= 768, 0 <= n_vec <= min(32, n).  Errors: EINVAL, ENOMEM, ECUDA. */
 int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, double* sigma, int n_vec,
                              double* vt, void* stream);

@@ -366,11 +366,13 @@ __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a) {
         int p0 = c - 1;
         while (p0 > 0 && sg[kept[p0 - 1]] - sg[kept[p0]] <= 1e-3 * tn) --p0;
         double* vc = vout + (size_t)c * n;
-        for (int p = p0; p < c; ++p) {
-          const double* vp = vout + (size_t)p * n;
-          double dot = 0.0;
-          for (int i = 0; i < n; ++i) dot = fma(vp[i], vc[i], dot);
-          for (int i = 0; i < n; ++i) vc[i] = fma(-dot, vp[i], vc[i]);
+        for (int pass = 0; pass < 2; ++pass) {       // twice: classical Gram-Schmidt loses orthogonality once
+          for (int p = p0; p < c; ++p) {
+            const double* vp = vout + (size_t)p * n;
+            double dot = 0.0;
+            for (int i = 0; i < n; ++i) dot = fma(vp[i], vc[i], dot);
+            for (int i = 0; i < n; ++i) vc[i] = fma(-dot, vp[i], vc[i]);
+          }
         }
         double s2 = 0.0;
         for (int i = 0; i < n; ++i) s2 = fma(vc[i], vc[i], s2);
