@@ -145,10 +145,17 @@ def test_ising_chi16_parity_auto_route(torch, L, beta, h, n):
 
 
 def test_routes_agree_at_L1024(torch):
-    # the headline lattice: one trajectory through each route
-    a = gpu_run(1024, 16, 1, seed_for(2), beta=0.44, first=1, svd=mctrg.SVD_JACOBI)
-    b = gpu_run(1024, 16, 1, seed_for(2), beta=0.44, first=1)
-    assert a[2][0] == b[2][0] == 1
-    assert abs(a[1][0] - b[1][0]) <= 1e-10 * abs(a[1][0])
+    # the headline lattice: one trajectory through each route.  Both routes
+    # flag the same trajectories; an unflagged one agrees to the parity
+    # tolerance, a flagged one (kept and dropped values of a near-degenerate
+    # cluster: the result depends on the basis chosen inside the cluster) to
+    # the size of that basis freedom's effect, checked loosely
+    a = gpu_run(1024, 16, 2, seed_for(2), beta=0.44, svd=mctrg.SVD_JACOBI)
+    b = gpu_run(1024, 16, 2, seed_for(2), beta=0.44)
+    np.testing.assert_array_equal(a[3], b[3])
+    np.testing.assert_array_equal(a[2], b[2])
+    for t in range(2):
+        tol = 1e-10 if a[3][t] == 0 else 1e-6
+        assert abs(a[1][t] - b[1][t]) <= tol * abs(a[1][t])
     f = ising.onsager_minus_beta_f(0.44)
-    assert abs(b[1][0] / 1024 ** 2 - f) < 2e-3
+    assert np.all(np.abs(b[1] / 1024 ** 2 - f) < 2e-3)
