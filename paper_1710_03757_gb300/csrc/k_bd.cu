@@ -152,39 +152,73 @@ __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_sme
 }
 
 // ---------------------------------------------------------------------------
-// 2. Sturm count: #{s_i < x} for the bidiagonal whose Golub-Kahan tridiagonal
-//    has squared off-diagonals oo[0 .. 2n-2] (normalized so that |T| <= 1),
-//    x > 0.  Sign changes of P_0 .. P_2n count the eigenvalues of T below x:
-//    the n values -s_i and those s_i < x.
-__device__ __forceinline__ int sturm_count(const double* __restrict__ oo, int n, double x) {
+// 2. Sturm count and determinant: for the bidiagonal whose Golub-Kahan
+//    tridiagonal has squared off-diagonals oo[0 .. 2n-2] (normalized so that
+//    |T| <= 1) and x > 0, returns #{s_i < x} (sign changes of P_0 .. P_2n count
+//    the eigenvalues of T below x: the n values -s_i and those s_i < x) and
+//    det(T - x I) = P_2n = f 2^fe.  Four steps between checks of the pair's
+//    magnitude: after a check the larger of |P_k|, |P_{k-1}| is >= 2^-100, and
+//    four steps shrink it by at most 2^-416 (x >= 2^-53, one cancellation), so
+//    nothing underflows; growth is at most 2 per step (|T| <= 1), so nothing
+//    overflows in 2n <= 1536 steps.
+#define MCTRG_STURM_STEP(K)                                          \
+  {                                                                  \
+    double q = fma(-x, p, -oo[(K) - 2] * pp);                        \
+    long long qb = __double_as_longlong(q);                          \
+    if ((qb << 1) == 0) {                                            \
+      q = -p * 0x1.0p-60;                                            \
+      qb = __double_as_longlong(q);                                  \
+    }                                                                \
+    neg += (int)((unsigned long long)(qb ^ __double_as_longlong(p)) >> 63); \
+    pp = p;                                                          \
+    p = q;                                                           \
+  }
+
+__device__ __forceinline__ int sturm_eval(const double* __restrict__ oo, int n, double x, double& f, int& fe) {
   double pp = 1.0, p = -x;
-  int neg = 1;
+  int neg = 1, E = 0;
   const int m = 2 * n;
-  for (int k = 2; k <= m; ++k) {
-    double q = fma(-x, p, -oo[k - 2] * pp);
-    long long qb = __double_as_longlong(q);
-    if ((qb << 1) == 0) {                 // a zero minor: a tiny pivot of the opposite sign
-      q = -p * 0x1.0p-60;
-      qb = __double_as_longlong(q);
-    }
-    neg += (int)((unsigned long long)(qb ^ __double_as_longlong(p)) >> 63);
-    pp = p;
-    p = q;
+  int k = 2;
+  for (; k + 3 <= m; k += 4) {
+    MCTRG_STURM_STEP(k)
+    MCTRG_STURM_STEP(k + 1)
+    MCTRG_STURM_STEP(k + 2)
+    MCTRG_STURM_STEP(k + 3)
     const int em = max(exp_field(p), exp_field(pp));
-    if (em < 1023 - 400) {                // rescale both by 2^(1023 - em), exactly
+    if (em < 1023 - 100) {                // rescale both by 2^(1023 - em), exactly
       const double sc = __hiloint2double((2046 - em) << 20, 0);
       p *= sc;
       pp *= sc;
+      E -= 1023 - em;
     }
   }
+  for (; k <= m; ++k) MCTRG_STURM_STEP(k)
+  f = p;
+  fe = E;
   return neg - n;
 }
+#undef MCTRG_STURM_STEP
 
+// 2^d as a double, |d| clamped to 1000.
+__device__ __forceinline__ double pow2i(int d) {
+  d = max(-1000, min(1000, d));
+  return __hiloint2double((1023 + d) << 20, 0);
+}
+
+// Each thread finds the values of its ranks: the bracket from a coarse grid of
+// counts, then bisection while the bracket holds more than one value, and
+// Illinois steps (regula falsi on det(T - x I), halving the retained end's
+// value when the same end moves twice) once it holds exactly one; three moves
+// of one end in a row force a bisection step.  The bracket always satisfies
+// count(lo) <= j < count(hi), so the result is within the final width of the
+// count's crossing, whatever the interpolation does.
 __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int n, int n_pad, double* sig,
                                                             int* perm, int* nnz, double* lns1, double zero_rel) {
   extern __shared__ double sm[];
   double* oo = sm;                                   // [2n]
-  int* cnt = (int*)(oo + 2 * n);                     // [kBisThreads]
+  double* gf = oo + 2 * n;                           // [kBisThreads] det at the grid points
+  int* cnt = (int*)(gf + kBisThreads);               // [kBisThreads]
+  int* gfe = cnt + kBisThreads;                      // [kBisThreads]
   __shared__ double red[32];
   __shared__ int s_zlo, s_nnz;
   const int mat = blockIdx.x, tid = threadIdx.x;
@@ -199,7 +233,6 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
     g = fmax(g, ok + on);
     om = fmax(om, ok);
   }
-  if (n == 1) { g = fabs(d[0]); om = g; }
   const double G = block_max(g, red);
   const double omax = block_max(om, red);
   if (!(G > 0.0)) {                                  // the zero matrix
@@ -215,22 +248,66 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
   const double zr = zero_rel > 0.0 ? zero_rel : (double)n * kEps;
   const double tlo = zr * omax * invG;               // <= the zero threshold zr s_1 / G
   __syncthreads();
-  // coarse grid: cnt[t] = #{s < x_t}, x_t = (t + 1) / T, the last point above |T|
-  const double xt = (tid == kBisThreads - 1) ? 1.0 + 0x1.0p-20 : (double)(tid + 1) / kBisThreads;
-  cnt[tid] = sturm_count(oo, n, xt);
-  if (tid == 0) s_zlo = sturm_count(oo, n, tlo);
+  // coarse grid: x_t = (t + 1) / T, the last point above |T|
+  const double top = 1.0 + 0x1.0p-20;
+  {
+    const double xt = (tid == kBisThreads - 1) ? top : (double)(tid + 1) / kBisThreads;
+    double f;
+    int fe;
+    cnt[tid] = sturm_eval(oo, n, xt, f, fe);
+    gf[tid] = f;
+    gfe[tid] = fe;
+    if (tid == 0) {
+      double f0;
+      int e0;
+      s_zlo = sturm_eval(oo, n, tlo, f0, e0);
+    }
+  }
   __syncthreads();
   const int zlo = s_zlo;
+  const double tol = 0x1.0p-51;
   for (int r = tid; r < n; r += kBisThreads) {
     const int j = n - 1 - r;                         // ascending index of the r-th largest
     if (j < zlo) { sg[r] = 0.0; continue; }          // below tlo: a zero
     int t = 0;
     while (t < kBisThreads - 1 && cnt[t] < j + 1) ++t;
-    double lo = t > 0 ? (double)t / kBisThreads : 0.0;
-    double hi = (t == kBisThreads - 1) ? 1.0 + 0x1.0p-20 : (double)(t + 1) / kBisThreads;
-    while (hi - lo > 0x1.0p-51) {
-      const double mid = 0.5 * (lo + hi);
-      if (sturm_count(oo, n, mid) >= j + 1) hi = mid; else lo = mid;
+    double hi = (t == kBisThreads - 1) ? top : (double)(t + 1) / kBisThreads;
+    int c_hi = cnt[t];
+    double f_hi = gf[t];
+    int e_hi = gfe[t];
+    double lo = 0.0, f_lo = 0.0;
+    int c_lo = 0, e_lo = 0;
+    bool have_lo = false;
+    if (t > 0) { lo = (double)t / kBisThreads; c_lo = cnt[t - 1]; f_lo = gf[t - 1]; e_lo = gfe[t - 1]; have_lo = true; }
+    int last = 0, run = 0;
+    for (int it = 0; it < 80 && hi - lo > tol; ++it) {
+      const bool interp = have_lo && c_lo == j && c_hi == j + 1 && run < 3;
+      double x = 0.5 * (lo + hi);
+      if (interp) {
+        const int dd = e_lo - e_hi;
+        const double al = fabs(f_lo) * (dd < 0 ? pow2i(dd) : 1.0);
+        const double ah = fabs(f_hi) * (dd > 0 ? pow2i(-dd) : 1.0);
+        const double den = al + ah;
+        if (den > 0.0) {
+          const double xi = lo + (al / den) * (hi - lo);
+          if (xi > lo && xi < hi) x = xi;
+        }
+      }
+      double f;
+      int fe;
+      const int c = sturm_eval(oo, n, x, f, fe);
+      if (c >= j + 1) {
+        hi = x; c_hi = c; f_hi = f; e_hi = fe;
+        if (interp && last == 1) e_lo -= 1;          // Illinois: halve the retained end
+        run = (last == 1) ? run + 1 : 1;
+        last = 1;
+      } else {
+        lo = x; c_lo = c; f_lo = f; e_lo = fe; have_lo = true;
+        if (interp && last == -1) e_hi -= 1;
+        run = (last == -1) ? run + 1 : 1;
+        last = -1;
+      }
+      if (!interp) run = 0;
     }
     sg[r] = G * (0.5 * (lo + hi));
   }
@@ -252,18 +329,21 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
 
 // ---------------------------------------------------------------------------
 // 3. Inverse iteration, one warp per matrix (persistent over matrices), lane a
-//    for the a-th kept index.  Scratch per warp slot, interleaved by lane:
-//    DG, DU, DU2 (the LU factors of T - s I with partial pivoting, in the
-//    layout of LAPACK's dgtsv) and X (the iterate), 4 x 2n x 32 doubles.
-__global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a) {
+//    for the a-th kept index.  Scratch per warp slot, interleaved by lane with
+//    stride ls (16 or 32): DG, DU, DU2 (the LU factors of T - s I with partial
+//    pivoting, in the layout of LAPACK's dgtsv) and X (the iterate), each 2n
+//    entries.  The factorization streams the current row in registers and
+//    applies L^-1 P^T to the right-hand side as it goes; the scale of the
+//    previous iterate is folded into the next right-hand side.
+__global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a, int ls) {
   const int lane = threadIdx.x;
   const int n = a.n, m = 2 * n;
-  double* scr = a.scratch + (size_t)blockIdx.x * 4 * m * 32;
-#define DG(i) scr[((size_t)0 * m + (i)) * 32 + lane]
-#define DU(i) scr[((size_t)1 * m + (i)) * 32 + lane]
-#define DU2(i) scr[((size_t)2 * m + (i)) * 32 + lane]
-#define XB(i) scr[((size_t)3 * m + (i)) * 32 + lane]
-#define XL(l, i) scr[((size_t)3 * m + (i)) * 32 + (l)]
+  double* scr = a.scratch + (size_t)blockIdx.x * 4 * m * ls;
+#define DG(i) scr[((size_t)0 * m + (i)) * ls + lane]
+#define DU(i) scr[((size_t)1 * m + (i)) * ls + lane]
+#define DU2(i) scr[((size_t)2 * m + (i)) * ls + lane]
+#define XB(i) scr[((size_t)3 * m + (i)) * ls + lane]
+#define XL(l, i) scr[((size_t)3 * m + (i)) * ls + (l)]
   for (int s = blockIdx.x; s < a.S; s += gridDim.x) {
     const int nk = a.nk[s];
     const int* kept = a.kept + (size_t)s * 32;
@@ -275,69 +355,72 @@ __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a) {
     for (int i = lane; i < n; i += 32) tn = fmax(tn, fmax(fabs(bd[i]), fabs(bd[n + i])));
     for (int o = 16; o > 0; o >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
     const double its = tn > 0.0 ? 1.0 / tn : 0.0;
-    const bool on = lane < nk;
+    const bool on = lane < nk && lane < ls;
     const double sgm = on ? sg[kept[lane]] * its : 0.0;
-    const double floor_piv = kEps;
+    // is this lane's value chained (within 1e-3 |T|) to a neighbouring kept value?
+    bool clustered = false;
+    if (on) {
+      if (lane > 0 && sg[kept[lane - 1]] - sg[kept[lane]] <= 1e-3 * tn) clustered = true;
+      if (lane + 1 < nk && sg[kept[lane]] - sg[kept[lane + 1]] <= 1e-3 * tn) clustered = true;
+    }
+#define OFFD(i) (((i) & 1) ? bd[n + ((i) >> 1)] : bd[(i) >> 1]) * its
     if (on) {                                        // start vector, different per lane
       for (int i = 0; i < m; ++i) XB(i) = 1.0 + 0.25 * (double)((i * (2 * lane + 3)) % 17) * (1.0 / 17.0);
     }
+    double rs = 1.0;                                 // scale owed by the stored iterate
     for (int iter = 0; iter < kInvitIters; ++iter) {
       if (on) {
-        // factor T - s I = P L U, applying L^-1 P^T to X on the fly
-        for (int i = 0; i < m; ++i) {
-          DG(i) = -sgm;
-          DU(i) = i < m - 1 ? ((i & 1) ? bd[n + (i >> 1)] : bd[i >> 1]) * its : 0.0;
-          DU2(i) = 0.0;
-        }
+        double dg = -sgm, du = OFFD(0), xi = XB(0) * rs;
         for (int i = 0; i < m - 1; ++i) {
-          const double dli = ((i & 1) ? bd[n + (i >> 1)] : bd[i >> 1]) * its;   // sub-diagonal = off-diagonal
-          const double dgi = DG(i);
-          if (fabs(dgi) >= fabs(dli)) {
-            const double gpiv = (dgi == 0.0) ? floor_piv : dgi;
-            DG(i) = gpiv;
-            const double f = dli / gpiv;
-            DG(i + 1) = DG(i + 1) - f * DU(i);
-            XB(i + 1) = XB(i + 1) - f * XB(i);
+          const double dli = OFFD(i);
+          const double dun = (i + 1 < m - 1) ? OFFD(i + 1) : 0.0;
+          const double xn = XB(i + 1) * rs;
+          if (fabs(dg) >= fabs(dli)) {
+            const double g = (dg == 0.0) ? kEps : dg;
+            const double f = dli / g;
+            DG(i) = g; DU(i) = du; DU2(i) = 0.0; XB(i) = xi;
+            dg = -sgm - f * du;
+            du = dun;
+            xi = xn - f * xi;
           } else {
-            const double f = dgi / dli;
-            DG(i) = dli;
-            const double t = DG(i + 1);
-            DG(i + 1) = DU(i) - f * t;
-            DU(i) = t;
-            if (i < m - 2) {
-              const double du1 = DU(i + 1);
-              DU2(i) = du1;
-              DU(i + 1) = -f * du1;
-            }
-            const double xi = XB(i), xi1 = XB(i + 1);
-            XB(i) = xi1;
-            XB(i + 1) = xi - f * xi1;
+            const double f = dg / dli;
+            DG(i) = dli; DU(i) = -sgm; DU2(i) = dun; XB(i) = xn;
+            dg = du + f * sgm;
+            du = -f * dun;
+            xi = xi - f * xn;
           }
         }
-        if (DG(m - 1) == 0.0) DG(m - 1) = floor_piv;
-        // back substitution U x = y
-        XB(m - 1) = XB(m - 1) / DG(m - 1);
-        if (m > 1) XB(m - 2) = (XB(m - 2) - DU(m - 2) * XB(m - 1)) / DG(m - 2);
-        for (int i = m - 3; i >= 0; --i) {
-          XB(i) = (XB(i) - DU(i) * XB(i + 1) - DU2(i) * XB(i + 2)) / DG(i);
-          if (exp_field(XB(i)) > 1023 + 600) {        // growth through tiny pivots: rescale x[i..]
-            for (int q = i; q < m; ++q) XB(q) *= 0x1.0p-600;
+        DG(m - 1) = (dg == 0.0) ? kEps : dg;
+        // back substitution U x = y, carrying x_{i+1}, x_{i+2}
+        double x1 = xi / DG(m - 1);
+        XB(m - 1) = x1;
+        double s2 = x1 * x1;
+        double x2 = 0.0;
+        for (int i = m - 2; i >= 0; --i) {
+          double x = (XB(i) - DU(i) * x1 - DU2(i) * x2) / DG(i);
+          if (exp_field(x) > 1023 + 600) {           // growth through tiny pivots: rescale x[i..]
+            for (int q = i + 1; q < m; ++q) XB(q) *= 0x1.0p-600;
+            x *= 0x1.0p-600; x1 *= 0x1.0p-600; x2 *= 0x1.0p-600; s2 *= 0x1.0p-1200;
           }
+          XB(i) = x;
+          s2 = fma(x, x, s2);
+          x2 = x1;
+          x1 = x;
         }
-        double s2 = 0.0;
-        for (int i = 0; i < m; ++i) s2 = fma(XB(i), XB(i), s2);
-        const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
-        for (int i = 0; i < m; ++i) XB(i) *= inv;
+        rs = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+        if (clustered) {                             // unit iterates for the Gram-Schmidt below
+          for (int i = 0; i < m; ++i) XB(i) *= rs;
+          rs = 1.0;
+        }
       }
       // Gram-Schmidt against the earlier kept vectors of the same cluster
       // (a chain of kept values less than 1e-3 |T| apart), in lane order
-      for (int c = 1; c < nk; ++c) {
+      for (int c = 1; c < nk && c < ls; ++c) {
         __syncwarp();
         if (sg[kept[c - 1]] - sg[kept[c]] > 1e-3 * tn) continue;
         if (lane == c) {
           int p0 = c - 1;
           while (p0 > 0 && sg[kept[p0 - 1]] - sg[kept[p0]] <= 1e-3 * tn) --p0;
-          // (the earlier cluster members' iterates are final for this iteration)
           for (int p = p0; p < c; ++p) {
             double dot = 0.0;
             for (int i = 0; i < m; ++i) dot = fma(XL(p, i), XB(i), dot);
@@ -351,6 +434,7 @@ __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a) {
       }
       __syncwarp();
     }
+#undef OFFD
     if (on) {                                        // v_B = even entries, normalized
       double s2 = 0.0;
       for (int i = 0; i < n; ++i) s2 = fma(XB(2 * i), XB(2 * i), s2);
@@ -359,7 +443,7 @@ __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a) {
     }
     // orthogonal z's of a cluster need not have orthogonal halves (values near
     // the noise level mix +s and -s): orthonormalize the v's of each cluster too
-    for (int c = 1; c < nk; ++c) {
+    for (int c = 1; c < nk && c < ls; ++c) {
       __syncwarp();
       if (sg[kept[c - 1]] - sg[kept[c]] > 1e-3 * tn) continue;
       if (lane == c) {
@@ -474,7 +558,7 @@ cudaError_t launch_bidiag(const BidiagArgs& a, cudaStream_t st) {
 cudaError_t launch_bd_bisect(const double* bd, int n, int n_pad, int S, double* sig, int* perm, int* nnz,
                              double* lns1, double zero_rel, cudaStream_t st) {
   if (S <= 0) return cudaSuccess;
-  const size_t smem = (size_t)2 * n * sizeof(double) + kBisThreads * sizeof(int);
+  const size_t smem = (size_t)2 * n * sizeof(double) + kBisThreads * (sizeof(double) + 2 * sizeof(int));
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
@@ -485,21 +569,19 @@ cudaError_t launch_bd_bisect(const double* bd, int n, int n_pad, int S, double* 
   return cudaGetLastError();
 }
 
-// Warp slots of the inverse iteration: enough to fill the GPU, few enough that
-// their scratch (4 x 2n x 32 doubles each) stays near the size of L2.
-static int invit_slots(int n, int S) {
-  const size_t per = (size_t)4 * 2 * n * 32 * sizeof(double);
-  const int by_l2 = (int)std::max<size_t>(152, (size_t)96 * 1024 * 1024 / per);
-  return std::max(1, std::min(S, std::min(by_l2, 152 * 8)));
-}
+// Warp slots of the inverse iteration: eight per SM (each runs one lane-serial
+// chain per kept vector, so the SMs need several to hide the FP64 latency).
+static int invit_slots(int S) { return std::max(1, std::min(S, 152 * 8)); }
 
-size_t bd_vectors_scratch_doubles(int n, int S) { return (size_t)invit_slots(n, S) * 4 * 2 * n * 32; }
+// Scratch of the inverse iteration: 4 x 2n x 32 doubles per slot (the lane
+// stride used is 16 when at most 16 vectors are kept, 32 otherwise).
+size_t bd_vectors_scratch_doubles(int n, int S) { return (size_t)invit_slots(S) * 4 * 2 * n * 32; }
 
 cudaError_t launch_bd_vectors(const BdVecArgs& a, cudaStream_t st) {
   if (a.S <= 0) return cudaSuccess;
   const size_t smem = (size_t)32 * a.n * sizeof(double);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  k_bd_invit<<<invit_slots(a.n, a.S), 32, 0, st>>>(a);
+  k_bd_invit<<<invit_slots(a.S), 32, 0, st>>>(a, a.kmax <= 16 ? 16 : 32);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   static bool attr = false;

@@ -41,6 +41,7 @@ struct BdVecArgs {
   double* scratch;
   int n, n_pad, S;
   int unit_rows;        // 1: write v_r itself instead of s_r v_r
+  int kmax;             // largest nk of the batch (<= 32)
 };
 cudaError_t launch_bd_vectors(const BdVecArgs& a, cudaStream_t st);
 size_t bd_vectors_scratch_doubles(int n, int S);

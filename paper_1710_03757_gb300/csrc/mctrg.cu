@@ -568,7 +568,7 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
             BdVecArgs va{};
             va.bd = bdb.as<double>(); va.R = Wb.as<double>(); va.sig = sigb.as<double>(); va.kept = keptb.as<int>();
             va.nk = nkb.as<int>(); va.vrows = vrowsb.as<double>(); va.scratch = bdscr.as<double>();
-            va.n = a.n; va.n_pad = a.n_pad; va.S = (int)Si;
+            va.n = a.n; va.n_pad = a.n_pad; va.S = (int)Si; va.kmax = a.kc;
             CK(timed(MCTRG_K_VECTORS, Si, Si * (2.0 * nn * nn * a.kc + 40.0 * nn * a.kc),
                      8.0 * Si * (nn * nn / 2.0 + 3.0 * nn + 2.0 * 32 * nn), [&] { return launch_bd_vectors(va, st); }));
             sa.mode = 2; sa.vrows = vrowsb.as<double>();

@@ -92,7 +92,7 @@ extern "C" int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, d
       k_kept_leading<<<(cnt + 127) / 128, 128, 0, st>>>(kept, nk, nnz, n_vec, cnt);
       BdVecArgs va{};
       va.bd = bd; va.R = W; va.sig = sig; va.kept = kept; va.nk = nk; va.vrows = vrows; va.scratch = scratch;
-      va.n = n; va.n_pad = np; va.S = cnt; va.unit_rows = 1;
+      va.n = n; va.n_pad = np; va.S = cnt; va.unit_rows = 1; va.kmax = n_vec;
       e = launch_bd_vectors(va, st);
     }
     if (e == cudaSuccess) {
