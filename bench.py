@@ -38,6 +38,9 @@ FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) of one 256 x 256 matrix in k_jacobi_warp, from the ncu capture
 # summarized in profiles/k_jacobi_warp_n256_ising_L32_chi16.md (2.66 GB for 128 matrices)
 JACOBI_DRAM_BYTES_PER_MATRIX_N256 = 2.658e9 / 128
+# DRAM bytes (read + write) of one 256 x 256 matrix in k_bidiag, from the ncu capture
+# summarized in profiles/k_bidiag_n256_ising_L32_chi16.md (None until captured)
+BIDIAG_DRAM_BYTES_PER_MATRIX_N256 = None
 
 
 def measured_peaks():
@@ -371,14 +374,19 @@ def main():
     dom = max(range(mctrg.K_COUNT), key=lambda k: stats[k].ms)
     ds = stats[dom]
     peaks, peak_src = measured_peaks()
-    if dom in (mctrg.K_JACOBI, mctrg.K_SAMPLE, mctrg.K_FORM_XY, mctrg.K_GEMM, mctrg.K_TRACE) and wl["precision"] == 0:
+    flop_classes = (mctrg.K_BIDIAG, mctrg.K_JACOBI, mctrg.K_VECTORS, mctrg.K_SAMPLE, mctrg.K_FORM_XY,
+                    mctrg.K_GEMM, mctrg.K_TRACE)
+    if dom in flop_classes and ds.flops_alg > 0 and wl["precision"] == 0:
         achieved = ds.flops_alg / (ds.ms / 1000.0) / 1e12 if ds.ms > 0 else 0.0
         peak = FP64_NOMINAL_TFLOPS
+        per_matrix = {mctrg.K_JACOBI: JACOBI_DRAM_BYTES_PER_MATRIX_N256,
+                      mctrg.K_BIDIAG: BIDIAG_DRAM_BYTES_PER_MATRIX_N256}.get(dom)
         roof = {"bound": "alu", "kernel": mctrg.KERNEL_NAMES[dom], "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": "nominal FP64 (DFMA) rate of GB300; the pool's DFMA probe measured 1.01 TFLOP/s",
-                "traffic": (JACOBI_DRAM_BYTES_PER_MATRIX_N256 * ds.items / max(1, ds.launches)
-                            if dom == mctrg.K_JACOBI and wl["chi"] == 16 else None),
+                "peak_source": "nominal FP64 (DFMA) rate of GB300, 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz; "
+                               "the FP64 GEMM of this workload runs at 1.25 TFLOP/s",
+                "traffic": (per_matrix * ds.items / max(1, ds.launches)
+                            if per_matrix and wl["chi"] == 16 else None),
                 "traffic_note": "bytes per launch, scaled from the per-matrix DRAM bytes of the ncu capture",
                 "launches": ds.launches, "avg_launch_ms": ds.ms / max(1, ds.launches),
                 "alg_flops_per_launch": ds.flops_alg / max(1, ds.launches)}

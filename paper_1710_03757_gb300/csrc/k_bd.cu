@@ -288,6 +288,36 @@ __device__ __forceinline__ int sturm_eval(const double* __restrict__ oo, int n, 
 }
 #undef MCTRG_STURM_STEP
 
+// The same count in FP32 (FP64 runs at 1/64 of the FP32 rate on GB300).  Its
+// rounding perturbs each off-diagonal and the shift x relatively (the terms
+// are products, no absolute error enters), so it is the exact count for a
+// matrix whose singular values are within a relative 2n 2^-23 of B's; it
+// serves to narrow a bracket that FP64 counts then verify.  The pair is
+// rescaled every step (x >= 2^-53 shrinks it by at most 2^-77 a step).
+__device__ __forceinline__ int sturm_count_f32(const float* __restrict__ oo, int n, float x) {
+  float pp = 1.0f, p = -x;
+  int neg = 1;
+  const int m = 2 * n;
+  for (int k = 2; k <= m; ++k) {
+    float q = fmaf(-x, p, -oo[k - 2] * pp);
+    int qb = __float_as_int(q);
+    if ((qb << 1) == 0) {
+      q = -p * 0x1.0p-30f;
+      qb = __float_as_int(q);
+    }
+    neg += (int)((unsigned)(qb ^ __float_as_int(p)) >> 31);
+    pp = p;
+    p = q;
+    const int em = max((__float_as_int(p) >> 23) & 0xff, (__float_as_int(pp) >> 23) & 0xff);
+    if (em < 127 - 40) {
+      const float sc = __int_as_float((254 - em) << 23);
+      p *= sc;
+      pp *= sc;
+    }
+  }
+  return neg - n;
+}
+
 // 2^d as a double, |d| clamped to 1000.
 __device__ __forceinline__ double pow2i(int d) {
   d = max(-1000, min(1000, d));
@@ -310,6 +340,7 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
   double* gf = oo + 2 * n;                           // [kBisThreads] det at the grid points
   int* cnt = (int*)(gf + kBisThreads);               // [kBisThreads]
   int* gfe = cnt + kBisThreads;                      // [kBisThreads]
+  float* oof = (float*)(gfe + kBisThreads);          // [2n] oo in FP32
   __shared__ double red[32];
   __shared__ double s_f0;
   __shared__ int s_zlo, s_nnz, s_e0;
@@ -336,6 +367,7 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
   for (int k = tid; k < 2 * n - 1; k += kBisThreads) {
     const double ok = ((k & 1) ? e[k >> 1] : d[k >> 1]) * invG;
     oo[k] = ok * ok;
+    oof[k] = (float)(ok * ok);
   }
   const double zr = zero_rel > 0.0 ? zero_rel : (double)n * kEps;
   const double tlo = zr * omax * invG;               // <= the zero threshold zr s_1 / G
@@ -376,6 +408,29 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
       lo = (double)t / kBisThreads; c_lo = cnt[t - 1]; f_lo = gf[t - 1]; e_lo = gfe[t - 1]; have_lo = true;
     } else if (tlo > 0.0 && tlo < hi) {              // the lowest bin starts at the zero bound
       lo = tlo; c_lo = zlo; f_lo = s_f0; e_lo = s_e0; have_lo = true;
+    }
+    // FP32 narrowing: bisect (geometrically across decades) to a relative width
+    // of 2^-16, widen by 2^-12 on each side, and keep the result only if FP64
+    // counts confirm it
+    if (have_lo && lo > 0x1.0p-100) {
+      float lo32 = (float)lo, hi32 = (float)hi;
+      for (int it = 0; it < 48 && hi32 > lo32 * (1.0f + 0x1.0p-16f); ++it) {
+        const float x = (hi32 > 2.0f * lo32) ? sqrtf(lo32 * hi32) : 0.5f * (lo32 + hi32);
+        if (!(x > lo32 && x < hi32)) break;
+        if (sturm_count_f32(oof, n, x) >= j + 1) hi32 = x; else lo32 = x;
+      }
+      const double lw = fmax(lo, (double)lo32 * (1.0 - 0x1.0p-12));
+      const double hw = fmin(hi, (double)hi32 * (1.0 + 0x1.0p-12));
+      if (lw > lo || hw < hi) {
+        double fl2, fh2;
+        int el2, eh2;
+        const int cl2 = lw > lo ? sturm_eval(oo, n, lw, fl2, el2) : c_lo;
+        const int ch2 = hw < hi ? sturm_eval(oo, n, hw, fh2, eh2) : c_hi;
+        if (cl2 <= j && ch2 >= j + 1) {
+          if (lw > lo) { lo = lw; c_lo = cl2; f_lo = fl2; e_lo = el2; }
+          if (hw < hi) { hi = hw; c_hi = ch2; f_hi = fh2; e_hi = eh2; }
+        }
+      }
     }
     int last = 0, run = 0;
     for (int it = 0; it < 80 && hi - lo > tol; ++it) {
@@ -669,7 +724,7 @@ cudaError_t launch_bidiag(const BidiagArgs& a, cudaStream_t st) {
 cudaError_t launch_bd_bisect(const double* bd, int n, int n_pad, int S, double* sig, int* perm, int* nnz,
                              double* lns1, double zero_rel, cudaStream_t st) {
   if (S <= 0) return cudaSuccess;
-  const size_t smem = (size_t)2 * n * sizeof(double) + kBisThreads * (sizeof(double) + 2 * sizeof(int));
+  const size_t smem = (size_t)2 * n * (sizeof(double) + sizeof(float)) + kBisThreads * (sizeof(double) + 2 * sizeof(int));
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
