@@ -78,7 +78,134 @@ __device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >
 //    row i > k applies both: a = A[i][:] - v_i w, y = tauR a.u, a -= y u, and
 //    hands column k+1 of the result to step k+1.  The trailing matrix is read
 //    twice and written once per step (the column dots w, the fused pass).
-//    Lane l of a warp holds the columns l, l + 32, ... of a row in registers.
+//    Lane l holds the trailing columns k+1+l, k+1+l+32, ... of a row in
+//    registers; the number of live 32-column chunks, QL, is a template
+//    argument chosen per step, so no FMA is issued for a finished column.  A
+//    warp takes up to four rows at a time and reduces their dots together.
+
+// 4-value warp sum: on return lanes 0, 8, 16, 24 hold the sums of p0, p1, p2, p3.
+__device__ __forceinline__ double reduce4(double p0, double p1, double p2, double p3, int lane) {
+  const bool hi16 = lane & 16, hi8 = lane & 8;
+  double q0 = hi16 ? p2 : p0, q1 = hi16 ? p3 : p1;
+  const double r0 = hi16 ? p0 : p2, r1 = hi16 ? p1 : p3;
+  q0 += __shfl_xor_sync(0xffffffffu, r0, 16);
+  q1 += __shfl_xor_sync(0xffffffffu, r1, 16);
+  double t = hi8 ? q1 : q0;
+  const double tr = hi8 ? q0 : q1;
+  t += __shfl_xor_sync(0xffffffffu, tr, 8);
+  t += __shfl_xor_sync(0xffffffffu, t, 4);
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  return t;
+}
+
+struct BdStep {
+  double* A;
+  const double* vcol;
+  const double* wv;
+  const double* uv;
+  double* wpart;
+  int n, k, lane, warp;
+};
+
+// w pass: per-warp partial sums sum_{i>k} v_i A[i][c] over the warp's rows.
+template <int QL>
+__device__ __forceinline__ void bd_w_pass(const BdStep& s) {
+  constexpr int NW = kBdThreads / 32;
+  const int n = s.n, c0 = s.k + 1 + s.lane;
+  double acc[QL];
+#pragma unroll
+  for (int q = 0; q < QL; ++q) acc[q] = 0.0;
+  for (int i = s.k + 1 + s.warp; i < n; i += NW) {
+    const double vi = s.vcol[i];
+    const double* row = s.A + (size_t)i * n;
+#pragma unroll
+    for (int q = 0; q < QL; ++q)
+      if (c0 + 32 * q < n) acc[q] = fma(vi, row[c0 + 32 * q], acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < QL; ++q)
+    if (c0 + 32 * q < n) s.wpart[s.warp * n + c0 + 32 * q] = acc[q];
+}
+
+// fused pass: rows i > k, four per warp; returns this warp's sum of the new
+// column k+1 squared below the diagonal (valid in lane 0).
+template <int QL>
+__device__ __forceinline__ double bd_fused_pass(const BdStep& s, double taur, double* vcol_out) {
+  constexpr int NW = kBdThreads / 32;
+  constexpr int RPW = QL <= 8 ? 4 : (QL <= 16 ? 2 : 1);   // rows per warp and pass (register budget)
+  const int n = s.n, k = s.k, lane = s.lane, c0 = k + 1 + lane;
+  double wr[QL], ur[QL];
+#pragma unroll
+  for (int q = 0; q < QL; ++q) {
+    const bool in = c0 + 32 * q < n;
+    wr[q] = in ? s.wv[c0 + 32 * q] : 0.0;
+    ur[q] = in ? s.uv[c0 + 32 * q] : 0.0;
+  }
+  double nsq = 0.0;
+  for (int i0 = k + 1 + RPW * s.warp; i0 < n; i0 += RPW * NW) {
+    double av[RPW][QL];
+    double y[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const int i = i0 + r;
+      y[r] = 0.0;
+      const double vi = i < n ? s.vcol[i] : 0.0;
+      const double* row = s.A + (size_t)i * n;
+#pragma unroll
+      for (int q = 0; q < QL; ++q) {
+        av[r][q] = 0.0;
+        if (i < n && c0 + 32 * q < n) {
+          av[r][q] = fma(-vi, wr[q], row[c0 + 32 * q]);
+          y[r] = fma(av[r][q], ur[q], y[r]);
+        }
+      }
+    }
+    double yr[4] = {0.0, 0.0, 0.0, 0.0};
+    if (taur != 0.0) {
+      const double t = reduce4(y[0], y[1], y[2], y[3], lane);
+      yr[0] = taur * __shfl_sync(0xffffffffu, t, 0);
+      yr[1] = taur * __shfl_sync(0xffffffffu, t, 8);
+      yr[2] = taur * __shfl_sync(0xffffffffu, t, 16);
+      yr[3] = taur * __shfl_sync(0xffffffffu, t, 24);
+    }
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const int i = i0 + r;
+      if (i >= n) break;
+      double* row = s.A + (size_t)i * n;
+#pragma unroll
+      for (int q = 0; q < QL; ++q) {
+        if (c0 + 32 * q < n) {
+          const double v = fma(-yr[r], ur[q], av[r][q]);
+          row[c0 + 32 * q] = v;
+          if (q == 0 && lane == 0) {
+            vcol_out[i] = v;                     // column k+1 for the next step
+            if (i > k + 1) nsq = fma(v, v, nsq);
+          }
+        }
+      }
+    }
+  }
+  return nsq;
+}
+
+template <int QL, int NQ>
+struct BdDispatch {
+  static __device__ __forceinline__ void w_pass(int ql, const BdStep& s) {
+    if (ql == QL) bd_w_pass<QL>(s); else BdDispatch<QL + 1, NQ>::w_pass(ql, s);
+  }
+  static __device__ __forceinline__ double fused(int ql, const BdStep& s, double taur, double* vo) {
+    if (ql == QL) return bd_fused_pass<QL>(s, taur, vo);
+    return BdDispatch<QL + 1, NQ>::fused(ql, s, taur, vo);
+  }
+};
+template <int NQ>
+struct BdDispatch<NQ + 1, NQ> {
+  static __device__ __forceinline__ void w_pass(int, const BdStep&) {}
+  static __device__ __forceinline__ double fused(int, const BdStep&, double, double*) { return 0.0; }
+};
+
 template <int NQ>
 __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_smem) {
   extern __shared__ double sm[];
@@ -96,7 +223,6 @@ __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_sme
   const double* Mm = a.M + (size_t)mat * n * n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ double s_xn2;
-  // copy in; column 0 and its norm below the diagonal
   for (int e = tid; e < n * n; e += kBdThreads) A[e] = Mm[e];
   for (int e = tid; e < 3 * n; e += kBdThreads) bd[e] = 0.0;
   __syncthreads();
@@ -111,7 +237,10 @@ __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_sme
     if (tid == 0) s_xn2 = t;
   }
   __syncthreads();
+  BdStep st{A, vcol, wv, uv, wpart, n, 0, lane, warp};
   for (int k = 0; k < n; ++k) {
+    st.k = k;
+    const int ql = (n - k - 1 + 31) >> 5;     // live 32-column chunks right of column k
     // ---- left reflector from column k
     const double xn2 = s_xn2;
     const double alpha = vcol[k];
@@ -127,23 +256,7 @@ __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_sme
     __syncthreads();
     // ---- w = tau (A[k][:] + v^T A[k+1:, :]) on columns > k
     if (tau != 0.0) {
-      double acc[NQ];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
-      for (int i = k + 1 + warp; i < n; i += NW) {
-        const double vi = vcol[i];
-        const double* row = A + (size_t)i * n;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          const int jj = lane + 32 * q;
-          if (jj > k && jj < n) acc[q] = fma(vi, row[jj], acc[q]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const int jj = lane + 32 * q;
-        if (jj > k && jj < n) wpart[warp * n + jj] = acc[q];
-      }
+      BdDispatch<1, NQ>::w_pass(ql, st);
       __syncthreads();
       for (int jj = k + 1 + tid; jj < n; jj += kBdThreads) {
         double sum = A[(size_t)k * n + jj];
@@ -177,61 +290,16 @@ __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_sme
     if (tid == 0) { uv[k + 1] = 1.0; bd[n + k] = betar; bd[2 * n + k] = taur; }
     __syncthreads();
     // ---- fused pass over rows i > k
-    {
-      double wr[NQ], ur[NQ];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const int jj = lane + 32 * q;
-        const bool in = jj > k && jj < n;
-        wr[q] = in ? wv[jj] : 0.0;
-        ur[q] = in ? uv[jj] : 0.0;
-      }
-      const int hq = (k + 1) >> 5, hl = (k + 1) & 31;   // holder of column k+1
-      double nsq = 0.0;
-      for (int i = k + 1 + warp; i < n; i += NW) {
-        double* row = A + (size_t)i * n;
-        const double vi = vcol[i];
-        double av[NQ];
-        double y = 0.0;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          const int jj = lane + 32 * q;
-          av[q] = 0.0;
-          if (jj > k && jj < n) {
-            av[q] = fma(-vi, wr[q], row[jj]);
-            y = fma(av[q], ur[q], y);
-          }
-        }
-        if (taur != 0.0) {
-          for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-          y *= taur;
-        } else {
-          y = 0.0;
-        }
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          const int jj = lane + 32 * q;
-          if (jj > k && jj < n) {
-            const double r = fma(-y, ur[q], av[q]);
-            row[jj] = r;
-            if (q == hq && lane == hl) {
-              vcol[i] = r;                      // column k+1 for the next step
-              if (i > k + 1) nsq = fma(r, r, nsq);
-            }
-          }
-        }
-      }
-      nsq = __shfl_sync(0xffffffffu, nsq, hl);
-      __syncthreads();                          // everyone done with red / vcol reads
-      if (lane == 0) red[warp] = nsq;
-      __syncthreads();
-      if (tid == 0) {
-        double t = 0.0;
-        for (int w = 0; w < NW; ++w) t += red[w];
-        s_xn2 = t;
-      }
-      __syncthreads();
+    const double nsq = BdDispatch<1, NQ>::fused(ql, st, taur, vcol);
+    __syncthreads();                            // everyone done with red / vcol reads
+    if (lane == 0) red[warp] = nsq;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < NW; ++w) t += red[w];
+      s_xn2 = t;
     }
+    __syncthreads();
   }
   if (use_smem) {
     __syncthreads();
@@ -648,7 +716,6 @@ __global__ void k_bd_backtr(BdVecArgs a) {
   if (a0 < nk) {
     double* V0 = V + (size_t)a0 * n;
     const int na = min(4, nk - a0);
-    const bool hi16 = lane & 16, hi8 = lane & 8;
     for (int k = n - 3; k >= 0; --k) {
       const double taur = tauR[k];
       if (taur == 0.0) continue;
@@ -661,17 +728,7 @@ __global__ void k_bd_backtr(BdVecArgs a) {
         if (na > 2) p2 = fma(uj, V0[2 * n + j], p2);
         if (na > 3) p3 = fma(uj, V0[3 * n + j], p3);
       }
-      double q0 = hi16 ? p2 : p0, q1 = hi16 ? p3 : p1;
-      const double r0 = hi16 ? p0 : p2, r1 = hi16 ? p1 : p3;
-      q0 += __shfl_xor_sync(0xffffffffu, r0, 16);
-      q1 += __shfl_xor_sync(0xffffffffu, r1, 16);
-      double t = hi8 ? q1 : q0;
-      const double tr = hi8 ? q0 : q1;
-      t += __shfl_xor_sync(0xffffffffu, tr, 8);
-      t += __shfl_xor_sync(0xffffffffu, t, 4);
-      t += __shfl_xor_sync(0xffffffffu, t, 2);
-      t += __shfl_xor_sync(0xffffffffu, t, 1);
-      // lanes with bits (4, 3) = (h, l) now hold the dot of vector 2 h + l
+      const double t = reduce4(p0, p1, p2, p3, lane);
       const double w0 = taur * __shfl_sync(0xffffffffu, t, 0);
       const double w1 = taur * __shfl_sync(0xffffffffu, t, 8);
       const double w2 = taur * __shfl_sync(0xffffffffu, t, 16);
