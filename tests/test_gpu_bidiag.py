@@ -60,10 +60,11 @@ def _run(torch, A, nv):
     return sig.cpu().numpy(), (vt.cpu().numpy() if nv else None)
 
 
-@pytest.mark.parametrize("n", [2, 3, 16, 33, 64, 100, 256])
+@pytest.mark.parametrize("n", [2, 3, 16, 33, 64, 100, 256, 300, 600])
 @pytest.mark.parametrize("kind", ["gauss", "graded", "lowrank", "pairs"])
 def test_values_and_kept_vectors_against_lapack(torch, n, kind):
-    batch = 5 if n >= 256 else 12
+    # n = 300 and 600 take the 16- and 24-chunk register layouts of the reduction
+    batch = 2 if n > 256 else (5 if n == 256 else 12)
     nv = min(16, n)
     A = _matrices(n, batch, kind, seed=1000 + n * 7 + len(kind))
     sg, V = _run(torch, A, nv)
