@@ -69,7 +69,8 @@ extern "C" {
  * the tensor cores, singular values below min(sqrt(n) u, 1/64) s_1 (u the
  * operand unit roundoff of the mode) are that arithmetic's noise and count
  * as zeros.  Levels whose GEMM shape the tensor-core kernel does not cover
- * (matrix side other than 256) use the FP64 GEMM and the FP64 threshold. */
+ * (matrix side not a multiple of 256, or above 1024) use the FP64 GEMM and
+ * the FP64 threshold. */
 typedef enum { MCTRG_FP64 = 0, MCTRG_TF32 = 1, MCTRG_BF16 = 2, MCTRG_TF32X3 = 3, MCTRG_BF16X3 = 4 } mctrg_precision;
 
 typedef struct {
@@ -94,7 +95,7 @@ typedef struct {
  *           (8/3) n^3 + O(n^2) flops whatever the rank.
  *   AUTO    BIDIAG where the matrices can have full rank (n >= 64 and the
  *           plaquette's inner dimension d^2 >= n / 2), JACOBI elsewhere.
- * BIDIAG covers n <= 768 (chi <= 27); larger levels take JACOBI. */
+ * BIDIAG covers n <= 1024 (chi <= 32); larger levels take JACOBI. */
 typedef enum { MCTRG_SVD_AUTO = 0, MCTRG_SVD_JACOBI = 1, MCTRG_SVD_BIDIAG = 2 } mctrg_svd_route;
 
 /* Estimate of Z from n trajectories (Sec. III Eq. infiniteEnsemble, Sec. V Eq.
@@ -247,7 +248,7 @@ int mctrg_svd_batched_noalloc(const double* M, int n, int64_t batch, double* sig
  * cluster's subspace; vectors of values at the noise level (a few 2^-52 n |M|
  * and below: the numerical null space) are not determined and carry no
  * guarantee.  Allocates and frees its working memory.
- * 2 <= n <= 768, 0 <= n_vec <= min(32, n).  Errors: EINVAL, ENOMEM, ECUDA. */
+ * 2 <= n <= 1024, 0 <= n_vec <= min(32, n).  Errors: EINVAL, ENOMEM, ECUDA. */
 int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, double* sigma, int n_vec,
                              double* vt, void* stream);
 

@@ -697,17 +697,18 @@ __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a, int ls) {
 }
 
 // ---------------------------------------------------------------------------
-// 4. v = H_0 H_1 ... H_{n-3} v_B, one CTA per matrix, vectors in shared
-//    memory, 4 vectors per warp (warps independent: no block barrier inside
-//    the reflector loop).  The four dot products of a warp are reduced
-//    together: one exchange halves four values to two, a second to one, then
-//    three butterfly steps finish the sum.
-__global__ void k_bd_backtr(BdVecArgs a) {
-  extern __shared__ double V[];                      // [32][n]
-  const int n = a.n, s = blockIdx.x;
+// 4. v = H_0 H_1 ... H_{n-3} v_B, one CTA of 4 warps per (matrix, group of 16
+//    kept vectors), the group in shared memory, 4 vectors per warp (warps
+//    independent: no block barrier inside the reflector loop).  The four dot
+//    products of a warp are reduced together (reduce4).
+constexpr int kBtGroup = 16;
+__global__ void __launch_bounds__(128) k_bd_backtr(BdVecArgs a) {
+  extern __shared__ double V[];                      // [kBtGroup][n]
+  const int n = a.n, s = blockIdx.x, g0 = blockIdx.y * kBtGroup;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nk = a.nk[s];
-  double* vrow = a.vrows + (size_t)s * 32 * n;
+  const int nk = min(a.nk[s] - g0, kBtGroup);        // vectors of this group
+  if (nk <= 0) return;
+  double* vrow = a.vrows + ((size_t)s * 32 + g0) * n;
   for (int e = threadIdx.x; e < nk * n; e += blockDim.x) V[e] = vrow[e];
   __syncthreads();
   const double* R = a.R + (size_t)s * n * n;
@@ -744,7 +745,7 @@ __global__ void k_bd_backtr(BdVecArgs a) {
     }
   }
   __syncthreads();
-  const int* kept = a.kept + (size_t)s * 32;
+  const int* kept = a.kept + (size_t)s * 32 + g0;
   const double* sg = a.sig + (size_t)s * a.n_pad;
   for (int e = threadIdx.x; e < nk * n; e += blockDim.x) vrow[e] = a.unit_rows ? V[e] : sg[kept[e / n]] * V[e];
 }
@@ -775,6 +776,7 @@ cudaError_t launch_bidiag(const BidiagArgs& a, cudaStream_t st) {
   if (a.n <= 256) return launch_bidiag_nq<8>(a, st);
   if (a.n <= 512) return launch_bidiag_nq<16>(a, st);
   if (a.n <= 768) return launch_bidiag_nq<24>(a, st);
+  if (a.n <= 1024) return launch_bidiag_nq<32>(a, st);
   return cudaErrorInvalidValue;
 }
 
@@ -792,19 +794,24 @@ cudaError_t launch_bd_bisect(const double* bd, int n, int n_pad, int S, double* 
   return cudaGetLastError();
 }
 
-// Warp slots of the inverse iteration: eight per SM (each runs one lane-serial
-// chain per kept vector, so the SMs need several to hide the FP64 latency).
-static int invit_slots(int S) { return std::max(1, std::min(S, 152 * 8)); }
+// Warp slots of the inverse iteration: up to eight per SM (each runs one
+// lane-serial chain per kept vector, so the SMs need several to hide the FP64
+// latency), and no more than 512 MB of scratch (4 x 2n x 32 doubles each).
+static int invit_slots(int n, int S) {
+  const size_t per = (size_t)4 * 2 * n * 32 * sizeof(double);
+  const int by_mem = (int)std::max<size_t>(152, ((size_t)512 << 20) / per);
+  return std::max(1, std::min(S, std::min(152 * 8, by_mem)));
+}
 
-// Scratch of the inverse iteration: 4 x 2n x 32 doubles per slot (the lane
-// stride used is 16 when at most 16 vectors are kept, 32 otherwise).
-size_t bd_vectors_scratch_doubles(int n, int S) { return (size_t)invit_slots(S) * 4 * 2 * n * 32; }
+// Scratch of the inverse iteration (the lane stride used is 16 when at most 16
+// vectors are kept, 32 otherwise).
+size_t bd_vectors_scratch_doubles(int n, int S) { return (size_t)invit_slots(n, S) * 4 * 2 * n * 32; }
 
 cudaError_t launch_bd_vectors(const BdVecArgs& a, cudaStream_t st) {
   if (a.S <= 0) return cudaSuccess;
-  const size_t smem = (size_t)32 * a.n * sizeof(double);
+  const size_t smem = (size_t)kBtGroup * a.n * sizeof(double);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  k_bd_invit<<<invit_slots(a.S), 32, 0, st>>>(a, a.kmax <= 16 ? 16 : 32);
+  k_bd_invit<<<invit_slots(a.n, a.S), 32, 0, st>>>(a, a.kmax <= 16 ? 16 : 32);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   static bool attr = false;
@@ -812,7 +819,8 @@ cudaError_t launch_bd_vectors(const BdVecArgs& a, cudaStream_t st) {
     cudaFuncSetAttribute(k_bd_backtr, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  k_bd_backtr<<<a.S, 256, smem, st>>>(a);
+  const dim3 grid((unsigned)a.S, (unsigned)((std::max(1, a.kmax) + kBtGroup - 1) / kBtGroup));
+  k_bd_backtr<<<grid, 128, smem, st>>>(a);
   return cudaGetLastError();
 }
 

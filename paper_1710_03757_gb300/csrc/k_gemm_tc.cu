@@ -10,8 +10,9 @@
 // square.  The FP32 result times the two scales is written in FP64, already
 // matricized for the next level, for the FP64 SVD.
 //
-// Kernel: one CTA of 128 threads per (tensor, 128-row tile of the output).
-// The accumulator (128 rows x n <= 256 FP32 columns) lives in tensor memory.
+// Kernel: one CTA of 128 threads per (tensor, 128-row tile, 256-column tile
+// of the output); n a multiple of 256 up to 1024 (chi = 16 ... 32).
+// The accumulator (128 rows x 256 FP32 columns) lives in tensor memory.
 // Warp 0 lane 0 loads 128-byte-wide K slices of both operands with TMA
 // (128-byte swizzle) into a ring of shared-memory stages; warp 1 lane 0
 // issues tcgen05.mma (K = 32 bytes per instruction, four per slice) and
@@ -195,13 +196,15 @@ __global__ void __launch_bounds__(128, 1)
   const int n = a.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t it = blockIdx.x;
-  const int mt = blockIdx.y;
+  const int mt = blockIdx.y;                            // 128-row tile of the output
+  const int nt = blockIdx.z;                            // 256-column tile of the output
+  constexpr int NT = 256;
   constexpr int kElems = KIND == 0 ? 32 : 64;           // elements per 128-byte row
   const int KB = a.K / kElems;
-  const uint32_t a_bytes = 128u * 128u, b_bytes = (uint32_t)n * 128u;
+  const uint32_t a_bytes = 128u * 128u, b_bytes = (uint32_t)NT * 128u;
   const uint32_t part = a_bytes + b_bytes;
   const uint32_t stage_bytes = (a.passes == 3 ? 2u : 1u) * part;
-  const uint32_t ncols = n <= 32 ? 32u : (n <= 64 ? 64u : (n <= 128 ? 128u : 256u));
+  const uint32_t ncols = NT;
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -220,8 +223,8 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // producer: one 128-byte K slice of A (this tile's 128 rows) and B (all n rows) per stage
-    const int ya = (int)(it * n + mt * 128), yb = (int)(it * n);
+    // producer: one 128-byte K slice of A (this tile's 128 rows) and B (this tile's 256 rows) per stage
+    const int ya = (int)(it * n + mt * 128), yb = (int)(it * n + nt * NT);
     int issued = 0;
     for (int kb = 0; kb < KB; ++kb) {
       const int s = kb % stages, round = kb / stages;
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(128, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    const uint32_t idesc = umma_idesc(KIND, 128, n);
+    const uint32_t idesc = umma_idesc(KIND, 128, NT);
     for (int kb = 0; kb < KB; ++kb) {
       const int s = kb % stages, round = kb / stages;
       if (!mbar_wait(&full_bar[s], round & 1)) { atomicOr(&s_fail, 1); break; }
@@ -278,13 +281,13 @@ __global__ void __launch_bounds__(128, 1)
     if (par < 0) par = tensor_parity(a.L, a.level_new, item % a.Nnew);
     double* Mo = a.M + it * (int64_t)n * n;
     const int al = r / D, be = r - al * D;
-    for (int c0 = 0; c0 < n; c0 += 32) {
+    for (int c0 = 0; c0 < NT; c0 += 32) {
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
       if (r < n) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int cc = c0 + j;
+          const int cc = nt * NT + c0 + j;
           const int de = cc / D, ga = cc - de * D;
           const double val = (double)__uint_as_float(v[j]) * sc;
           if (par == 0) Mo[(int64_t)r * n + cc] = val;
@@ -331,7 +334,7 @@ static bool encode_map(CUtensorMap* m, const void* base, int kind, uint64_t rows
 }
 
 bool gemm_tc_supported(int n, int K, int kind) {
-  return n == 256 && K % (kind == 0 ? 32 : 64) == 0 && K >= 64;
+  return n % 256 == 0 && n <= 1024 && K % (kind == 0 ? 32 : 64) == 0 && K >= 64;
 }
 
 cudaError_t launch_convert_scaled(const double* src, int64_t per_item, int64_t n_items, int kind, void* hi, void* lo,
@@ -348,22 +351,22 @@ cudaError_t launch_gemm_tc(const GemmTcArgs& a, int kind, const void* Xh, const 
   if (!gemm_tc_supported(a.n, a.K, kind)) return cudaErrorInvalidValue;
   CUtensorMap mAh, mBh, mAl, mBl;
   const uint64_t rows = (uint64_t)a.n_items * a.n;
-  if (!encode_map(&mAh, Xh, kind, rows, a.K, 128) || !encode_map(&mBh, Yh, kind, rows, a.K, (uint32_t)a.n))
+  if (!encode_map(&mAh, Xh, kind, rows, a.K, 128) || !encode_map(&mBh, Yh, kind, rows, a.K, 256))
     return cudaErrorInvalidValue;
   if (a.passes == 3) {
-    if (!encode_map(&mAl, Xl, kind, rows, a.K, 128) || !encode_map(&mBl, Yl, kind, rows, a.K, (uint32_t)a.n))
+    if (!encode_map(&mAl, Xl, kind, rows, a.K, 128) || !encode_map(&mBl, Yl, kind, rows, a.K, 256))
       return cudaErrorInvalidValue;
   } else {
     mAl = mAh;
     mBl = mBh;
   }
-  const uint32_t part = 128u * 128u + (uint32_t)a.n * 128u;
+  const uint32_t part = 128u * 128u + 256u * 128u;
   const uint32_t stage_bytes = (a.passes == 3 ? 2u : 1u) * part;
   int stages = (int)((200u * 1024u) / stage_bytes);
   if (stages > kTcMaxStages) stages = kTcMaxStages;
   if (stages < 1) return cudaErrorInvalidValue;
   const size_t smem = (size_t)stages * stage_bytes + 1024;
-  dim3 grid((unsigned)a.n_items, (unsigned)(a.n / 128));
+  dim3 grid((unsigned)a.n_items, (unsigned)(a.n / 128), (unsigned)(a.n / 256));
   if (kind == 0) {
     cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_gemm_tc<0><<<grid, 128, smem, st>>>(mAh, mBh, mAl, mBl, a, stages);

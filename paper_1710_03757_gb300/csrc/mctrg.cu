@@ -272,7 +272,7 @@ int mctrg_ctx::init_from_device_tensor(int D0, int L_, int chi_) {
 
 // SVD route of a level whose n x n matrices are X Yt^T with inner dimension K.
 bool mctrg_ctx::use_bidiag(int n, int K) const {
-  if (opt.svd == MCTRG_SVD_JACOBI || n > 768) return false;   // vectors' shared tile: 32 n doubles
+  if (opt.svd == MCTRG_SVD_JACOBI || n > 1024) return false;
   if (opt.svd == MCTRG_SVD_BIDIAG) return n >= 2;
   return n >= 64 && 2 * K >= n;
 }

@@ -60,7 +60,7 @@ using namespace mctrg;
 
 extern "C" int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, double* sigma, int n_vec,
                                         double* vt, void* stream) {
-  if (!M || !sigma || n < 2 || n > 768 || batch < 1 || batch > (1 << 30)) return MCTRG_EINVAL;
+  if (!M || !sigma || n < 2 || n > 1024 || batch < 1 || batch > (1 << 30)) return MCTRG_EINVAL;
   if (n_vec < 0 || n_vec > 32 || n_vec > n || (n_vec > 0 && !vt)) return MCTRG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const int np = n + (n & 1);

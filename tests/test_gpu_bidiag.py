@@ -60,11 +60,11 @@ def _run(torch, A, nv):
     return sig.cpu().numpy(), (vt.cpu().numpy() if nv else None)
 
 
-@pytest.mark.parametrize("n", [2, 3, 16, 33, 64, 100, 256, 300, 600])
+@pytest.mark.parametrize("n", [2, 3, 16, 33, 64, 100, 256, 300, 600, 1024])
 @pytest.mark.parametrize("kind", ["gauss", "graded", "lowrank", "pairs"])
 def test_values_and_kept_vectors_against_lapack(torch, n, kind):
-    # n = 300 and 600 take the 16- and 24-chunk register layouts of the reduction
-    batch = 2 if n > 256 else (5 if n == 256 else 12)
+    # n = 300, 600 and 1024 take the 16-, 24- and 32-chunk register layouts of the reduction
+    batch = (1 if n > 600 else 2) if n > 256 else (5 if n == 256 else 12)
     nv = min(16, n)
     A = _matrices(n, batch, kind, seed=1000 + n * 7 + len(kind))
     sg, V = _run(torch, A, nv)
@@ -126,6 +126,15 @@ def test_ising_parity_bidiag(torch, beta, h, L, chi, n):
     seed = 991 + L
     gpu = gpu_run(L, chi, n, seed, beta=beta, h=h, svd=mctrg.SVD_BIDIAG)
     orc = run_many(Problem(ising.site_tensor(beta, h), L, chi), seed, 0, n)
+    compare(gpu, orc, min_ok=0.5)
+
+
+def test_chi32_parity_n1024_levels(torch):
+    # chi = 32: the deepest levels are 1024 x 1024 (32-chunk reduction, vectors in
+    # two back-transformation groups of 16)
+    T0 = generic_tensor(2, seed=9)
+    gpu = gpu_run(8, 32, 6, 31, T0=T0)
+    orc = run_many(Problem(T0, 8, 32), 31, 0, 6, workers=6)
     compare(gpu, orc, min_ok=0.5)
 
 

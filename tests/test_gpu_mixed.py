@@ -57,3 +57,13 @@ def test_generic_tensor_mixed():
     st, est, ln, _ = run(mctrg.MCTRG_TF32X3, L=8, chi=16, n=16, T0=T0)
     assert st == 0 and st0 == 0
     assert np.median(np.abs(ln - ln0) / np.abs(ln0)) <= 1e-6
+
+
+def test_chi32_tensor_core_levels():
+    # chi = 32: the 1024 x 1024 plaquette GEMMs run on the tensor cores in
+    # 128 x 256 output tiles (four column tiles per tensor)
+    st0, est0, ln0, sg0 = run(mctrg.MCTRG_FP64, L=16, chi=32, n=4)
+    st, est, ln, sg = run(mctrg.MCTRG_TF32X3, L=16, chi=32, n=4)
+    assert st0 == 0 and st == 0
+    np.testing.assert_array_equal(sg, sg0)
+    assert np.median(np.abs(ln - ln0) / np.abs(ln0)) <= 1e-6
