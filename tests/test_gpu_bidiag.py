@@ -129,12 +129,18 @@ def test_ising_parity_bidiag(torch, beta, h, L, chi, n):
     compare(gpu, orc, min_ok=0.5)
 
 
-def test_chi32_parity_n1024_levels(torch):
+@pytest.mark.parametrize("case", ["ising", "generic3"])
+def test_chi32_parity_n1024_levels(torch, case):
     # chi = 32: the deepest levels are 1024 x 1024 (32-chunk reduction, vectors in
-    # two back-transformation groups of 16)
-    T0 = generic_tensor(2, seed=9)
-    gpu = gpu_run(8, 32, 6, 31, T0=T0)
-    orc = run_many(Problem(T0, 8, 32), 31, 0, 6, workers=6)
+    # two back-transformation groups of 16).  (A D = 2 generic tensor at this
+    # chi keeps values below 1e-7 s_1 in every trajectory: all flagged.)
+    if case == "ising":
+        T0, L, n = ising.site_tensor(0.3, 0.0), 8, 8
+        gpu = gpu_run(L, 32, n, 31, beta=0.3)
+    else:
+        T0, L, n = generic_tensor(3, seed=9), 8, 6
+        gpu = gpu_run(L, 32, n, 31, T0=T0)
+    orc = run_many(Problem(T0, L, 32), 31, 0, n, workers=n)
     compare(gpu, orc, min_ok=0.5)
 
 
