@@ -104,18 +104,19 @@ def draw(w, chi, u):
     return sorted(kept), flags
 
 
-def truncate(s, chi, uniforms_fn, n_rows):
+def truncate(s, chi, uniforms_fn, n_rows, zero_scale=1.0):
     """Stochastic truncation of one descending spectrum s (length n_rows).
 
     Returns (kept indices, reweighted kept values s_i / r_i, flags, used),
     where used says whether uniforms were consumed.  Values at or below the
-    zero threshold tau = n_rows * 2^-52 * s_1 count as exact zeros (the
-    paper samples among the nonzero singular values, Sec. II).
+    zero threshold tau = zero_scale * n_rows * 2^-52 * s_1 count as exact
+    zeros (the paper samples among the nonzero singular values, Sec. II;
+    zero_scale = 1 is the default reading of "nonzero").
     """
     s1 = s[0]
     if not s1 > 0.0:
         return [], np.zeros(0), 0, False
-    tau = n_rows * 2.0 ** -52 * s1
+    tau = zero_scale * n_rows * 2.0 ** -52 * s1
     flags = 0
     nnz = int(np.sum(s > tau))
     if nnz <= chi:

@@ -85,21 +85,22 @@ def contract(F3, F4, F2, F1):
 class Problem:
     """A lattice: L x L torus of identical site tensors T0 (legs l,u,r,d)."""
 
-    def __init__(self, T0, L, chi):
+    def __init__(self, T0, L, chi, zero_tol_scale=1.0):
         T0 = np.asarray(T0, dtype=np.float64)
         if T0.ndim != 4 or len(set(T0.shape)) != 1:
             raise ValueError("T0 must be D x D x D x D")
         if chi < 1:
             raise ValueError("chi >= 1")
         self.T0, self.L, self.chi = T0, int(L), int(chi)
+        self.zero_tol_scale = float(zero_tol_scale)   # multiplies the zero threshold (Sec. II "nonzero")
         self.levels = plan(self.L)
         self.n_levels = len(self.levels) - 1      # SVD levels: 0 .. 2m-1
 
 
-def _stochastic_chooser(seed, traj, level, tensor, chi):
+def _stochastic_chooser(seed, traj, level, tensor, chi, zero_scale=1.0):
     def choose(s, n_rows):
         uf = lambda c: philox.uniforms(seed, traj, level, tensor, c)
-        kept, st, flags, _ = truncate(s, chi, uf, n_rows)
+        kept, st, flags, _ = truncate(s, chi, uf, n_rows, zero_scale)
         return kept, st, flags
     return choose
 
@@ -119,7 +120,7 @@ def run_level(prob, k, tensors, shared, chooser_for):
         for par in (0, 1):
             s = svd(matricize(tensors[0], par))[1]
             if s[0] > 0:
-                nu = max(nu, int(np.sum(s / s[0] > n_rows * 2.0 ** -52)))
+                nu = max(nu, int(np.sum(s / s[0] > prob.zero_tol_scale * n_rows * 2.0 ** -52)))
         Dn = max(1, min(prob.chi, nu))
         exact = nu <= prob.chi
     else:
@@ -150,7 +151,7 @@ def run_trajectory(prob, seed, traj):
     lnacc = 0.0
     flags = 0
     for k in range(prob.n_levels):
-        chooser_for = lambda t, k=k: _stochastic_chooser(seed, traj, k, t, prob.chi)
+        chooser_for = lambda t, k=k: _stochastic_chooser(seed, traj, k, t, prob.chi, prob.zero_tol_scale)
         tensors, lnk, f, shared = run_level(prob, k, tensors, shared, chooser_for)
         lnacc += lnk
         flags |= f

@@ -122,3 +122,15 @@ def test_truncate_flags():
     u_edge = E[1, 1] / E[3, 1]
     kept, flags = draw(w, 1, [u_edge])
     assert flags & FLAG_DRAW_TIE
+
+
+def test_zero_threshold_scale():
+    # R5 with a scale: values at or below zero_scale * n * 2^-52 * s_1 are zeros.
+    # n = 4: tau = 8.9e-16 s_1 at scale 1, 8.9e-14 s_1 at scale 100
+    from oracle.sampler import truncate
+    s = np.array([1.0, 1e-14, 1e-20, 0.0])
+    kept, st, flags, used = truncate(s, 4, None, 4)
+    assert kept == [0, 1] and not used
+    kept, st, flags, used = truncate(s, 4, None, 4, zero_scale=100.0)
+    assert kept == [0] and not used
+    np.testing.assert_array_equal(st, [1.0])
