@@ -83,6 +83,11 @@ typedef struct {
     int profile;              /* 1: time every kernel launch with CUDA events on the
                                  context's stream (see mctrg_kernel_stats)             */
     int svd;                  /* mctrg_svd_route of the per-trajectory SVDs            */
+    double zero_tol_scale;    /* multiplies the zero threshold of every SVD: singular
+                                 values at or below scale * tau count as zeros
+                                 (Sec. II samples among the nonzero values; tau is
+                                 n 2^-52 s_1 in FP64, see mctrg_precision for the
+                                 mixed modes); 0 = 1, negative or non-finite: EINVAL */
 } mctrg_options;
 
 /* Route of the per-trajectory SVDs (Sec. II, Eq. exactSVD), both FP64 with

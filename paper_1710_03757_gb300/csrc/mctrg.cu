@@ -79,6 +79,7 @@ extern "C" int mctrg_create(const mctrg_options* opt, mctrg_ctx_t* out) {
   if (!opt || !out) return MCTRG_EINVAL;
   if (opt->precision < MCTRG_FP64 || opt->precision > MCTRG_BF16X3) return MCTRG_EINVAL;
   if (opt->svd < MCTRG_SVD_AUTO || opt->svd > MCTRG_SVD_BIDIAG) return MCTRG_EINVAL;
+  if (!(opt->zero_tol_scale >= 0.0) || !std::isfinite(opt->zero_tol_scale)) return MCTRG_EINVAL;
   *out = nullptr;
   int ndev = 0;
   CK(cudaGetDeviceCount(&ndev));
@@ -88,6 +89,7 @@ extern "C" int mctrg_create(const mctrg_options* opt, mctrg_ctx_t* out) {
   if (!c) return MCTRG_ENOMEM;
   c->opt = *opt;
   if (c->opt.max_sweeps <= 0) c->opt.max_sweeps = 40;
+  if (c->opt.zero_tol_scale == 0.0) c->opt.zero_tol_scale = 1.0;
   c->st = (cudaStream_t)opt->cuda_stream;
   if (c->opt.hbm_budget_bytes == 0) {
     size_t fr = 0, tot = 0;
@@ -199,6 +201,7 @@ int mctrg_ctx::init_from_device_tensor(int D0, int L_, int chi_) {
     ja.M = shM.as<double>(); ja.W = shW.as<double>(); ja.sig = shSig.as<double>();
     ja.perm = shPerm.as<int>(); ja.lns1 = shLns1.as<double>(); ja.nnz = shNnz.as<int>();
     ja.mflags = nullptr; ja.n = n; ja.n_pad = np; ja.S = 2; ja.max_sweeps = opt.max_sweeps;
+    ja.zero_rel = opt.zero_tol_scale * (double)n * 0x1.0p-52;
     CK(launch_jacobi(ja, st));
     int hn[2];
     double hl[2];
@@ -545,7 +548,8 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
                      [&] { return launch_gemm_f64(gm, st); }));
           }
           const double nn = a.n;
-          const double zero_rel = used_tc ? std::min(std::sqrt(nn) * tc_unit_roundoff(prec), 1.0 / 64.0) : 0.0;
+          const double zero_rel = opt.zero_tol_scale *
+              (used_tc ? std::min(std::sqrt(nn) * tc_unit_roundoff(prec), 1.0 / 64.0) : nn * 0x1.0p-52);
           SampleArgs sa{};
           sa.M = Mb.as<double>(); sa.sig = sigb.as<double>(); sa.nnz = nnzb.as<int>(); sa.Urows = nullptr;
           sa.n = a.n; sa.n_pad = a.n_pad; sa.chi = chi; sa.kc = a.kc; sa.stochastic = 1; sa.shared_svd = 0;
@@ -580,10 +584,8 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
             ja.perm = permb.as<int>(); ja.lns1 = ilns1.as<double>() + i0; ja.nnz = nnzb.as<int>();
             ja.mflags = iflags.as<uint32_t>() + i0; ja.n = a.n; ja.n_pad = a.n_pad; ja.S = (int)Si;
             ja.max_sweeps = opt.max_sweeps;
-            if (used_tc) {
-              ja.noise_u = tc_unit_roundoff(prec);
-              ja.zero_rel = zero_rel;
-            }
+            ja.zero_rel = zero_rel;
+            if (used_tc) ja.noise_u = tc_unit_roundoff(prec);
             CK(timed(MCTRG_K_JACOBI, Si, Si * ((8.0 / 3.0) * nn * nn * nn + 4.0 * nn * nn * a.kc),
                      8.0 * Si * (nn * nn + (double)a.n_pad * nn + 1.5 * a.n_pad), [&] { return launch_jacobi(ja, st); }));
             sa.mode = 0; sa.W = Wb.as<double>(); sa.perm = permb.as<int>();

@@ -38,7 +38,8 @@ class KernelStat(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("max_sweeps", ctypes.c_int),
-                ("max_chunk", ctypes.c_int), ("profile", ctypes.c_int), ("svd", ctypes.c_int)]
+                ("max_chunk", ctypes.c_int), ("profile", ctypes.c_int), ("svd", ctypes.c_int),
+                ("zero_tol_scale", ctypes.c_double)]
 
 
 class Estimate(ctypes.Structure):
@@ -135,9 +136,10 @@ def mctrg_options_default():
 
 
 def make_options(device=0, stream=None, precision=MCTRG_FP64, hbm_budget_bytes=0, max_sweeps=0,
-                 max_chunk=0, profile=0, svd=SVD_AUTO):
+                 max_chunk=0, profile=0, svd=SVD_AUTO, zero_tol_scale=0.0):
     o = mctrg_options_default()
     o.device, o.precision, o.profile, o.svd = int(device), int(precision), int(profile), int(svd)
+    o.zero_tol_scale = float(zero_tol_scale)
     o.cuda_stream = stream
     o.hbm_budget_bytes, o.max_sweeps, o.max_chunk = int(hbm_budget_bytes), int(max_sweeps), int(max_chunk)
     return o

@@ -130,6 +130,17 @@ def test_full_size_L1024_properties():
     assert abs(m[1][0] - b[1][0]) / abs(b[1][0]) < 1e-6
 
 
+@pytest.mark.parametrize("svd", [mctrg.SVD_JACOBI, mctrg.SVD_BIDIAG])
+def test_zero_tol_scale_parity(svd):
+    # a larger zero threshold (Sec. II samples among the "nonzero" values):
+    # the same scale on both sides gives the same trajectories
+    T0 = generic_tensor(2, seed=23)
+    seed, n, scale = 4321, 100, 1e9
+    gpu = gpu_run(8, 4, n, seed, T0=T0, svd=svd, zero_tol_scale=scale)
+    orc = run_many(Problem(T0, 8, 4, zero_tol_scale=scale), seed, 0, n)
+    assert compare(gpu, orc, min_ok=0.9) >= 0.9 * n
+
+
 def test_exact_path_L2():
     # chi = 4 >= every rank: no sampling, every trajectory equals Z
     for beta, h in ((0.44, 0.0), (0.3, 0.2)):
