@@ -142,3 +142,66 @@ def onsager_minus_beta_f_1d(beta):
     f = lambda t: math.log((1 + math.sqrt(max(0.0, 1 - (k * math.sin(t)) ** 2))) / 2)
     val, _ = quad(f, 0, math.pi / 2, limit=200, epsabs=1e-14, epsrel=1e-14)
     return math.log(2 * math.cosh(2 * K)) + val / math.pi
+
+
+# ---------------------------------------------------------------------------
+# The spins-on-bonds network of Sec. IV (Fig. 1): an L x L torus of tensors
+# whose legs carry the spins; the four spins on the legs of one tensor sit
+# around one plaquette of the (45-degree rotated) square lattice, and the
+# tensor holds the four nearest-neighbour bonds of that plaquette.  2 L^2
+# spins, 4 L^2 bonds (the L = 8 network is the paper's 128-spin lattice).
+# Each spin belongs to two tensors, so a field h enters as e^{beta h s / 2}
+# per leg.
+
+def bond_spin_tensor(beta, h=0.0):
+    """T[l,u,r,d] = exp(beta (s_l s_u + s_u s_r + s_r s_d + s_d s_l)
+                         + beta h (s_l + s_u + s_r + s_d) / 2), index 0 = spin +1."""
+    sp = np.array([1.0, -1.0])
+    l, u, r, d = np.meshgrid(sp, sp, sp, sp, indexing='ij')
+    return np.exp(beta * (l * u + u * r + r * d + d * l) + 0.5 * beta * h * (l + u + r + d))
+
+
+def bond_spin_brute_lnZ(L, beta, h=0.0):
+    """ln Z of the L x L spins-on-bonds torus by enumerating all 2^(2 L^2)
+    states, from the spin geometry alone: horizontal bond spins hs[y][x] (the
+    r leg of tensor (x, y) and l leg of (x+1, y)), vertical vs[y][x] (the d leg
+    of (x, y) and u leg of (x, y+1)); tensor (x, y) couples its four legs
+    around a plaquette."""
+    n = 2 * L * L
+    if n > 18:
+        raise ValueError("brute force limited to 2 L^2 <= 18")
+    idx = np.arange(1 << n, dtype=np.int64)
+    s = 1 - 2 * ((idx[:, None] >> np.arange(n)) & 1)
+    hs = s[:, :L * L].reshape(-1, L, L)            # [state, y, x]
+    vs = s[:, L * L:].reshape(-1, L, L)
+    E = np.zeros(len(idx))
+    M = s.sum(axis=1).astype(np.float64)
+    for y in range(L):
+        for x in range(L):
+            sl = hs[:, y, (x - 1) % L]
+            su = vs[:, (y - 1) % L, x]
+            sr = hs[:, y, x]
+            sd = vs[:, y, x]
+            E += sl * su + su * sr + sr * sd + sd * sl
+    return _logsumexp(beta * E + beta * h * M)
+
+
+def bond_spin_transfer_lnZ(L, beta, h=0.0):
+    """ln Z of the L x L spins-on-bonds torus as ln Tr(R^L), R the 2^L x 2^L
+    row transfer matrix R[(u_0..u_{L-1}), (d_0..d_{L-1})] = sum over the
+    horizontal bonds of the ring of L tensors (r of x = l of x+1, periodic)."""
+    if L > 10:
+        raise ValueError("transfer matrix limited to L <= 10")
+    T = bond_spin_tensor(beta, h)
+    # ring contraction: A[l_0, U..., r_x, D...] over the first x+1 tensors
+    A = T.transpose(0, 1, 3, 2)                     # [l0, u0, d0, r0]
+    for _ in range(1, L):
+        # A[l0, U, D, r] * T[r, u, r', d] -> [l0, (U, u), (D, d), r']
+        A = np.einsum('aUDr,rusd->aUuDds', A, T)
+        a, U, u, Dd, d, s_ = A.shape
+        A = A.reshape(a, U * u, Dd * d, s_)
+    R = np.einsum('aUDa->UD', A)
+    m = R.max()
+    ev = np.linalg.eigvals(R / m)
+    z = np.sum(ev.astype(np.complex128) ** L)
+    return float(L * math.log(m) + math.log(z.real))

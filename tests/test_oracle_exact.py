@@ -69,3 +69,36 @@ def test_site_tensor_rank_two():
     T = ising.site_tensor(0.44, 0.1)
     s = np.linalg.svd(T.reshape(4, 4), compute_uv=False)
     assert s[1] > 1e-3 * s[0] and s[2] < 1e-14 * s[0]
+
+
+# ---- the spins-on-bonds network of Sec. IV (Fig. 1) -------------------------
+
+@pytest.mark.parametrize("L,beta,h", [(2, 0.4, 0.0), (2, 0.7, 0.1), (3, 0.44, 0.0), (3, 0.3, -0.2)])
+def test_bond_spin_transfer_equals_brute_force(L, beta, h):
+    assert ising.bond_spin_transfer_lnZ(L, beta, h) == pytest.approx(ising.bond_spin_brute_lnZ(L, beta, h),
+                                                                     rel=1e-13)
+
+
+def test_bond_spin_beta0():
+    for L in (2, 3, 8):
+        assert ising.bond_spin_transfer_lnZ(L, 0.0) == pytest.approx(2 * L * L * math.log(2.0), rel=1e-14)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_bond_spin_network_trace(L):
+    # the tensor network of the bond-spin tensors (geometry of the network
+    # module, independent of the transfer matrix's ring contraction)
+    lev = plan(L)[0]
+    T = ising.bond_spin_tensor(0.5, 0.05)
+    assert math.log(network_trace([T] * lev.n, lev)) == pytest.approx(
+        ising.bond_spin_transfer_lnZ(L, 0.5, 0.05), rel=1e-13)
+
+
+def test_bond_spin_is_the_square_lattice():
+    # 2 L^2 spins of a (rotated) square lattice: ln Z per spin -> Onsager;
+    # at high temperature the 128-spin torus is within 1e-7 of the limit, in
+    # the ordered phase it exceeds it by ln 2 / N (the two ground states)
+    N = 128
+    assert ising.bond_spin_transfer_lnZ(8, 0.2) / N == pytest.approx(ising.onsager_minus_beta_f(0.2), abs=1e-7)
+    assert (ising.bond_spin_transfer_lnZ(8, 0.8) / N - math.log(2.0) / N ==
+            pytest.approx(ising.onsager_minus_beta_f(0.8), abs=1e-6))
