@@ -145,6 +145,15 @@ int mctrg_create(const mctrg_options* opt, mctrg_ctx_t* out);
  * Errors: EINVAL, ENOMEM, ECUDA. */
 int mctrg_init_lattice(mctrg_ctx_t ctx, double beta, double h, int L, int chi);
 
+/* The paper's own lattice (Sec. IV, Fig. 1): the Ising spins live on the
+ * bonds of the L x L tensor network (2 L^2 spins on a 45-degree rotated
+ * periodic square lattice; L = 8 is the paper's 128-spin network, six
+ * coarse-graining steps).  The tensor holds the four bonds around a plaquette:
+ * T[l,u,r,d] = exp(beta (s_l s_u + s_u s_r + s_r s_d + s_d s_l)
+ *                  + beta h (s_l + s_u + s_r + s_d) / 2), index 0 = spin +1.
+ * Arguments, limits and errors as mctrg_init_lattice. */
+int mctrg_init_bond_lattice(mctrg_ctx_t ctx, double beta, double h, int L, int chi);
+
 /* Same as mctrg_init_lattice with an arbitrary site tensor T0 (host pointer,
  * D^4 doubles, index order [l][u][r][d], row-major), 1 <= D <= 8, copied. */
 int mctrg_init_tensor(mctrg_ctx_t ctx, const double* T0, int D, int L, int chi);

@@ -204,6 +204,23 @@ cudaError_t launch_site_tensor(double beta, double h, double* T, cudaStream_t st
   return cudaGetLastError();
 }
 
+// Spins-on-bonds network (Sec. IV, Fig. 1): the legs carry the spins, and the
+// four spins around a tensor form a plaquette whose four bonds it holds:
+// T[l,u,r,d] = exp(beta (s_l s_u + s_u s_r + s_r s_d + s_d s_l)
+//                  + beta h (s_l + s_u + s_r + s_d) / 2)   (a spin is on two legs).
+__global__ void k_bond_tensor(double beta, double h, double* T) {
+  const int e = threadIdx.x;
+  if (e >= 16) return;
+  const double sl = (e >> 3) & 1 ? -1.0 : 1.0, su = (e >> 2) & 1 ? -1.0 : 1.0;
+  const double sr = (e >> 1) & 1 ? -1.0 : 1.0, sd = e & 1 ? -1.0 : 1.0;
+  T[e] = exp(beta * (sl * su + su * sr + sr * sd + sd * sl) + 0.5 * beta * h * (sl + su + sr + sd));
+}
+
+cudaError_t launch_bond_tensor(double beta, double h, double* T, cudaStream_t st) {
+  k_bond_tensor<<<1, 32, 0, st>>>(beta, h, T);
+  return cudaGetLastError();
+}
+
 __global__ void k_matricize2(const double* T, int D, double* out) {
   const int n = D * D;
   const int64_t tot = (int64_t)n * n;

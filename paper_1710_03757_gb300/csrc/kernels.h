@@ -106,6 +106,8 @@ cudaError_t launch_trace(const double* X, const double* Yt, int64_t K2, int64_t 
 
 // ---- small kernels -----------------------------------------------------------
 cudaError_t launch_site_tensor(double beta, double h, double* T, cudaStream_t st);
+// The spins-on-bonds tensor of the paper's Fig. 1 network (D = 2).
+cudaError_t launch_bond_tensor(double beta, double h, double* T, cudaStream_t st);
 // A and B matricizations of a raw tensor T[l][u][r][d] (D^4): out[0] = A, out[1] = B.
 cudaError_t launch_matricize2(const double* T, int D, double* out, cudaStream_t st);
 // lnacc[b] += sum_t ilns1[b*N+t] (if ilns1), tflags[b] |= OR_t iflags[b*N+t].

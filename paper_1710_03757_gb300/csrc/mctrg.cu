@@ -293,6 +293,17 @@ extern "C" int mctrg_init_lattice(mctrg_ctx_t c, double beta, double h, int L, i
   return c->init_from_device_tensor(2, L, chi);
 }
 
+extern "C" int mctrg_init_bond_lattice(mctrg_ctx_t c, double beta, double h, int L, int chi) {
+  if (!c) return MCTRG_EINVAL;
+  if (!is_pow2(L) || L > 65536 || chi < 1 || chi > 32 || !(beta >= 0.0) || !std::isfinite(beta) ||
+      !std::isfinite(h))
+    return MCTRG_EINVAL;
+  CK(cudaSetDevice(c->opt.device));
+  CK(c->T0.ensure(16 * sizeof(double)));
+  CK(launch_bond_tensor(beta, h, c->T0.as<double>(), c->st));
+  return c->init_from_device_tensor(2, L, chi);
+}
+
 extern "C" int mctrg_init_tensor(mctrg_ctx_t c, const double* T0, int D, int L, int chi) {
   if (!c || !T0) return MCTRG_EINVAL;
   if (!is_pow2(L) || L > 65536 || chi < 1 || chi > 32 || D < 1 || D > 8) return MCTRG_EINVAL;

@@ -18,7 +18,7 @@ FLAG_SPLIT_CLUSTER, FLAG_DRAW_TIE, FLAG_TINY_KEPT, FLAG_NOCONV = 1, 2, 4, 16
 
 # every symbol the headers declare (checked by the CPU test suite)
 EXPORTS = [
-    "mctrg_options_default", "mctrg_create", "mctrg_init_lattice", "mctrg_init_tensor",
+    "mctrg_options_default", "mctrg_create", "mctrg_init_lattice", "mctrg_init_bond_lattice", "mctrg_init_tensor",
     "mctrg_run", "mctrg_footprint", "mctrg_merge_estimates", "mctrg_destroy", "mctrg_strerror",
     "mctrg_server_create", "mctrg_server_submit", "mctrg_server_poll", "mctrg_server_wait",
     "mctrg_server_destroy", "mctrg_plan_level", "mctrg_philox_uniform", "mctrg_kernel_stats",
@@ -70,6 +70,7 @@ def lib():
             "mctrg_options_default": (c_int, [ctypes.POINTER(Options)]),
             "mctrg_create": (c_int, [ctypes.POINTER(Options), ctypes.POINTER(vp)]),
             "mctrg_init_lattice": (c_int, [vp, c_double, c_double, c_int, c_int]),
+            "mctrg_init_bond_lattice": (c_int, [vp, c_double, c_double, c_int, c_int]),
             "mctrg_init_tensor": (c_int, [vp, vp, c_int, c_int, c_int]),
             "mctrg_run": (c_int, [vp, i64, u64, u64, vp, vp, vp, ctypes.POINTER(Estimate)]),
             "mctrg_footprint": (c_int, [vp, i64, ctypes.POINTER(ctypes.c_size_t)]),
@@ -154,6 +155,11 @@ def mctrg_create(opts=None):
 
 def mctrg_init_lattice(ctx, beta, h, L, chi):
     return lib().mctrg_init_lattice(ctx, float(beta), float(h), int(L), int(chi))
+
+
+def mctrg_init_bond_lattice(ctx, beta, h, L, chi):
+    """The spins-on-bonds network of the paper's Fig. 1 (L = 8: 128 spins)."""
+    return lib().mctrg_init_bond_lattice(ctx, float(beta), float(h), int(L), int(chi))
 
 
 def mctrg_init_tensor(ctx, T0, D, L, chi):

@@ -1,0 +1,76 @@
+"""The paper's own lattice (Sec. IV, Fig. 1): Ising spins on the bonds of an
+L x L tensor network, L = 8 for the 128-spin network of Table 1.
+
+Per-trajectory parity with the oracle on the same Philox stream, the mean of
+Z~/Z against the exact transfer-matrix Z (unbiasedness, Sec. III), and the
+per-sample standard deviation of Z~/Z at the first Table 1 point (chi~ = 6,
+T = 1.5: 4.171e-2), which only a sampler drawing from the same p(e) with the
+same reweighting reproduces.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ising
+from oracle.trg import Problem, run_many
+from paper_1710_03757_gb300 import build, mctrg
+
+from test_gpu_parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+    mctrg.lib()
+
+
+def bond_run(L, chi, n, seed, beta, h=0.0, first=0):
+    ctx = mctrg.mctrg_create(mctrg.make_options())
+    try:
+        s = mctrg.mctrg_init_bond_lattice(ctx, beta, h, L, chi)
+        assert s == 0, mctrg.mctrg_strerror(s)
+        lnabs = np.zeros(n)
+        sign = np.zeros(n, dtype=np.int8)
+        flags = np.zeros(n, dtype=np.uint8)
+        st, est = mctrg.mctrg_run(ctx, n, seed, first, lnabs, sign, flags)
+        assert st in (mctrg.MCTRG_OK, mctrg.MCTRG_EDOMAIN), mctrg.mctrg_strerror(st)
+        return est, lnabs, sign, flags
+    finally:
+        mctrg.mctrg_destroy(ctx)
+
+
+@pytest.mark.parametrize("L,chi,T,h,n", [(4, 2, 1.5, 0.0, 300), (8, 6, 1.5, 0.0, 200),
+                                         (8, 6, 2.34826, 0.0, 200), (8, 4, 2.0, 0.1, 200)])
+def test_bond_lattice_parity(L, chi, T, h, n):
+    beta = 1.0 / T
+    seed = 0xB0D5 + L + chi
+    gpu = bond_run(L, chi, n, seed, beta, h)
+    orc = run_many(Problem(ising.bond_spin_tensor(beta, h), L, chi), seed, 0, n, workers=8)
+    compare(gpu, orc, min_ok=0.8)
+
+
+@pytest.mark.parametrize("L,chi,T,n", [(4, 3, 2.34826, 50000), (8, 12, 2.34826, 40000)])
+def test_bond_lattice_unbiased(L, chi, T, n):
+    beta = 1.0 / T
+    est, lnabs, sign, _ = bond_run(L, chi, n, 0x7AB1E + L, beta)
+    z = math.exp(ising.bond_spin_transfer_lnZ(L, beta) - est.ln_scale)
+    assert abs(est.mean_Z_scaled - z) <= 4 * est.se_Z_scaled
+
+
+def test_table1_first_point():
+    # 128 spins, chi~ = 6, T = 1.5: Table 1 gives a per-sample standard
+    # deviation of Z~/Z of 4.171e-2.  The distribution is multimodal (most of
+    # the mass in one mode, Fig. 2), so the estimate of the std converges
+    # slowly; the check is on its order (a factor 1.5 either way) and on the
+    # mean (unbiased within 4 standard errors).
+    beta = 1.0 / 1.5
+    n = 1 << 20
+    est, lnabs, sign, _ = bond_run(8, 6, n, 0x7AB1E, beta)
+    lnZ = ising.bond_spin_transfer_lnZ(8, beta)
+    zr = sign * np.exp(lnabs - lnZ)
+    mean, std = zr.mean(), zr.std(ddof=1)
+    assert abs(mean - 1.0) <= 4 * std / math.sqrt(n)
+    assert 4.171e-2 / 1.5 <= std <= 4.171e-2 * 1.5, std
