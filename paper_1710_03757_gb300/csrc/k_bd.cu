@@ -81,7 +81,8 @@ __device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >
 //    Lane l holds the trailing columns k+1+l, k+1+l+32, ... of a row in
 //    registers; the number of live 32-column chunks, QL, is a template
 //    argument chosen per step, so no FMA is issued for a finished column.  A
-//    warp takes up to four rows at a time and reduces their dots together.
+//    warp takes up to four rows at a time and reduces their dots together;
+//    the right reflector enters as us = sqrt(tauR) u (G = I - us us^T).
 
 // 4-value warp sum: on return lanes 0, 8, 16, 24 hold the sums of p0, p1, p2, p3.
 __device__ __forceinline__ double reduce4(double p0, double p1, double p2, double p3, int lane) {
@@ -128,13 +129,60 @@ __device__ __forceinline__ void bd_w_pass(const BdStep& s) {
     if (c0 + 32 * q < n) s.wpart[s.warp * n + c0 + 32 * q] = acc[q];
 }
 
-// fused pass: rows i > k, four per warp; returns this warp's sum of the new
-// column k+1 squared below the diagonal (valid in lane 0).
+// R consecutive rows i0 .. i0+R-1 (all < n) of the fused pass: a = A[i] - v_i w,
+// y = a.us (us = sqrt(tauR) u, so the right update is a -= y us), reduced for
+// the R rows together; returns this lane's share of the new column k+1 squared.
+template <int QL, int R>
+__device__ __forceinline__ double bd_rows(const BdStep& s, int i0, const double (&wr)[QL], const double (&ur)[QL],
+                                          double* vcol_out) {
+  const int n = s.n, k = s.k, lane = s.lane, c0 = k + 1 + lane;
+  double av[R][QL];
+  double y[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const double vi = s.vcol[i0 + r];
+    const double* row = s.A + (size_t)(i0 + r) * n;
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+      av[r][q] = 0.0;
+      if (c0 + 32 * q < n) {
+        av[r][q] = fma(-vi, wr[q], row[c0 + 32 * q]);
+        y[r] = fma(av[r][q], ur[q], y[r]);
+      }
+    }
+  }
+  const double t = reduce4(y[0], y[1], y[2], y[3], lane);
+  double yr[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) yr[r] = __shfl_sync(0xffffffffu, t, 8 * r);
+  double nsq = 0.0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = i0 + r;
+    double* row = s.A + (size_t)i * n;
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+      if (c0 + 32 * q < n) {
+        const double v = fma(-yr[r], ur[q], av[r][q]);
+        row[c0 + 32 * q] = v;
+        if (q == 0 && lane == 0) {
+          vcol_out[i] = v;                       // column k+1 for the next step
+          if (i > k + 1) nsq = fma(v, v, nsq);
+        }
+      }
+    }
+  }
+  return nsq;
+}
+
+// fused pass: rows i > k, RPW per warp (full groups), then the leftover rows of
+// the last group one at a time; returns this warp's sum of the new column k+1
+// squared below the diagonal (valid in lane 0).
 template <int QL>
-__device__ __forceinline__ double bd_fused_pass(const BdStep& s, double taur, double* vcol_out) {
+__device__ __forceinline__ double bd_fused_pass(const BdStep& s, double* vcol_out) {
   constexpr int NW = kBdThreads / 32;
   constexpr int RPW = QL <= 8 ? 4 : (QL <= 16 ? 2 : 1);   // rows per warp and pass (register budget)
-  const int n = s.n, k = s.k, lane = s.lane, c0 = k + 1 + lane;
+  const int n = s.n, k = s.k, c0 = k + 1 + s.lane;
   double wr[QL], ur[QL];
 #pragma unroll
   for (int q = 0; q < QL; ++q) {
@@ -143,50 +191,10 @@ __device__ __forceinline__ double bd_fused_pass(const BdStep& s, double taur, do
     ur[q] = in ? s.uv[c0 + 32 * q] : 0.0;
   }
   double nsq = 0.0;
-  for (int i0 = k + 1 + RPW * s.warp; i0 < n; i0 += RPW * NW) {
-    double av[RPW][QL];
-    double y[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-    for (int r = 0; r < RPW; ++r) {
-      const int i = i0 + r;
-      y[r] = 0.0;
-      const double vi = i < n ? s.vcol[i] : 0.0;
-      const double* row = s.A + (size_t)i * n;
-#pragma unroll
-      for (int q = 0; q < QL; ++q) {
-        av[r][q] = 0.0;
-        if (i < n && c0 + 32 * q < n) {
-          av[r][q] = fma(-vi, wr[q], row[c0 + 32 * q]);
-          y[r] = fma(av[r][q], ur[q], y[r]);
-        }
-      }
-    }
-    double yr[4] = {0.0, 0.0, 0.0, 0.0};
-    if (taur != 0.0) {
-      const double t = reduce4(y[0], y[1], y[2], y[3], lane);
-      yr[0] = taur * __shfl_sync(0xffffffffu, t, 0);
-      yr[1] = taur * __shfl_sync(0xffffffffu, t, 8);
-      yr[2] = taur * __shfl_sync(0xffffffffu, t, 16);
-      yr[3] = taur * __shfl_sync(0xffffffffu, t, 24);
-    }
-#pragma unroll
-    for (int r = 0; r < RPW; ++r) {
-      const int i = i0 + r;
-      if (i >= n) break;
-      double* row = s.A + (size_t)i * n;
-#pragma unroll
-      for (int q = 0; q < QL; ++q) {
-        if (c0 + 32 * q < n) {
-          const double v = fma(-yr[r], ur[q], av[r][q]);
-          row[c0 + 32 * q] = v;
-          if (q == 0 && lane == 0) {
-            vcol_out[i] = v;                     // column k+1 for the next step
-            if (i > k + 1) nsq = fma(v, v, nsq);
-          }
-        }
-      }
-    }
-  }
+  int i0 = k + 1 + RPW * s.warp;
+  for (; i0 + RPW <= n; i0 += RPW * NW) nsq += bd_rows<QL, RPW>(s, i0, wr, ur, vcol_out);
+  if (RPW > 1)
+    for (int i = i0; i < n && i < i0 + RPW; ++i) nsq += bd_rows<QL, 1>(s, i, wr, ur, vcol_out);
   return nsq;
 }
 
@@ -195,15 +203,15 @@ struct BdDispatch {
   static __device__ __forceinline__ void w_pass(int ql, const BdStep& s) {
     if (ql == QL) bd_w_pass<QL>(s); else BdDispatch<QL + 1, NQ>::w_pass(ql, s);
   }
-  static __device__ __forceinline__ double fused(int ql, const BdStep& s, double taur, double* vo) {
-    if (ql == QL) return bd_fused_pass<QL>(s, taur, vo);
-    return BdDispatch<QL + 1, NQ>::fused(ql, s, taur, vo);
+  static __device__ __forceinline__ double fused(int ql, const BdStep& s, double* vo) {
+    if (ql == QL) return bd_fused_pass<QL>(s, vo);
+    return BdDispatch<QL + 1, NQ>::fused(ql, s, vo);
   }
 };
 template <int NQ>
 struct BdDispatch<NQ + 1, NQ> {
   static __device__ __forceinline__ void w_pass(int, const BdStep&) {}
-  static __device__ __forceinline__ double fused(int, const BdStep&, double, double*) { return 0.0; }
+  static __device__ __forceinline__ double fused(int, const BdStep&, double*) { return 0.0; }
 };
 
 template <int NQ>
@@ -281,16 +289,19 @@ __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_sme
       betar = -copysign(sqrt(fma(ar, ar, yn2)), ar);
       taur = (betar - ar) / betar;
       const double scal = 1.0 / (ar - betar);
+      const double rt = sqrt(taur);               // G = I - us us^T with us = sqrt(tauR) u
       for (int jj = k + 2 + tid; jj < n; jj += kBdThreads) {
         const double u = uv[jj] * scal;
-        uv[jj] = u;
+        uv[jj] = rt * u;
         A[(size_t)k * n + jj] = u;              // kept for the back-transformation
       }
+    } else {
+      for (int jj = k + 2 + tid; jj < n; jj += kBdThreads) uv[jj] = 0.0;
     }
-    if (tid == 0) { uv[k + 1] = 1.0; bd[n + k] = betar; bd[2 * n + k] = taur; }
+    if (tid == 0) { uv[k + 1] = sqrt(taur); bd[n + k] = betar; bd[2 * n + k] = taur; }
     __syncthreads();
     // ---- fused pass over rows i > k
-    const double nsq = BdDispatch<1, NQ>::fused(ql, st, taur, vcol);
+    const double nsq = BdDispatch<1, NQ>::fused(ql, st, vcol);
     __syncthreads();                            // everyone done with red / vcol reads
     if (lane == 0) red[warp] = nsq;
     __syncthreads();
@@ -393,9 +404,9 @@ __device__ __forceinline__ double pow2i(int d) {
 }
 
 // Each thread finds the values of its ranks: the bracket from a coarse grid of
-// counts (the lowest bin starting at the zero bound), then bisection while the
-// bracket holds more than one value (geometric while it spans more than a
-// factor 2), and
+// FP32 counts (the lowest bin starting at the zero bound), narrowed with FP32
+// counts and verified with FP64 ones, then bisection while the bracket holds
+// more than one value (geometric while it spans more than a factor 2), and
 // Illinois steps (regula falsi on det(T - x I), halving the retained end's
 // value when the same end moves twice) once it holds exactly one; three moves
 // of one end in a row force a bisection step.  The bracket always satisfies
@@ -405,10 +416,8 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
                                                             int* perm, int* nnz, double* lns1, double zero_rel) {
   extern __shared__ double sm[];
   double* oo = sm;                                   // [2n]
-  double* gf = oo + 2 * n;                           // [kBisThreads] det at the grid points
-  int* cnt = (int*)(gf + kBisThreads);               // [kBisThreads]
-  int* gfe = cnt + kBisThreads;                      // [kBisThreads]
-  float* oof = (float*)(gfe + kBisThreads);          // [2n] oo in FP32
+  int* cnt = (int*)(oo + 2 * n);                     // [kBisThreads] FP32 grid counts
+  float* oof = (float*)(cnt + kBisThreads);          // [2n] oo in FP32
   __shared__ double red[32];
   __shared__ double s_f0;
   __shared__ int s_zlo, s_nnz, s_e0;
@@ -440,15 +449,11 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
   const double zr = zero_rel > 0.0 ? zero_rel : (double)n * kEps;
   const double tlo = zr * omax * invG;               // <= the zero threshold zr s_1 / G
   __syncthreads();
-  // coarse grid: x_t = (t + 1) / T, the last point above |T|
+  // coarse grid of FP32 counts: x_t = (t + 1) / T, the last point above |T|
   const double top = 1.0 + 0x1.0p-20;
   {
     const double xt = (tid == kBisThreads - 1) ? top : (double)(tid + 1) / kBisThreads;
-    double f;
-    int fe;
-    cnt[tid] = sturm_eval(oo, n, xt, f, fe);
-    gf[tid] = f;
-    gfe[tid] = fe;
+    cnt[tid] = sturm_count_f32(oof, n, (float)xt);
     if (tid == 0) {
       double f0;
       int e0;
@@ -463,46 +468,35 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
   for (int r = tid; r < n; r += kBisThreads) {
     const int j = n - 1 - r;                         // ascending index of the r-th largest
     if (j < zlo) { sg[r] = 0.0; continue; }          // below tlo: a zero
+    // FP32: the grid bin, then bisection (geometric across decades) to a
+    // relative width of 2^-16
     int t = 0;
     while (t < kBisThreads - 1 && cnt[t] < j + 1) ++t;
-    double hi = (t == kBisThreads - 1) ? top : (double)(t + 1) / kBisThreads;
-    int c_hi = cnt[t];
-    double f_hi = gf[t];
-    int e_hi = gfe[t];
-    double lo = 0.0, f_lo = 0.0;
-    int c_lo = 0, e_lo = 0;
-    bool have_lo = false;
-    if (t > 0) {
-      lo = (double)t / kBisThreads; c_lo = cnt[t - 1]; f_lo = gf[t - 1]; e_lo = gfe[t - 1]; have_lo = true;
-    } else if (tlo > 0.0 && tlo < hi) {              // the lowest bin starts at the zero bound
-      lo = tlo; c_lo = zlo; f_lo = s_f0; e_lo = s_e0; have_lo = true;
+    float lo32 = t > 0 ? (float)t / kBisThreads : (float)tlo;
+    float hi32 = (t == kBisThreads - 1) ? (float)top : (float)(t + 1) / kBisThreads;
+    for (int it = 0; it < 48 && hi32 > lo32 * (1.0f + 0x1.0p-16f); ++it) {
+      const float x = (hi32 > 2.0f * lo32) ? sqrtf(lo32 * hi32) : 0.5f * (lo32 + hi32);
+      if (!(x > lo32 && x < hi32)) break;
+      if (sturm_count_f32(oof, n, x) >= j + 1) hi32 = x; else lo32 = x;
     }
-    // FP32 narrowing: bisect (geometrically across decades) to a relative width
-    // of 2^-16, widen by 2^-12 on each side, and keep the result only if FP64
-    // counts confirm it
-    if (have_lo && lo > 0x1.0p-100) {
-      float lo32 = (float)lo, hi32 = (float)hi;
-      for (int it = 0; it < 48 && hi32 > lo32 * (1.0f + 0x1.0p-16f); ++it) {
-        const float x = (hi32 > 2.0f * lo32) ? sqrtf(lo32 * hi32) : 0.5f * (lo32 + hi32);
-        if (!(x > lo32 && x < hi32)) break;
-        if (sturm_count_f32(oof, n, x) >= j + 1) hi32 = x; else lo32 = x;
-      }
-      const double lw = fmax(lo, (double)lo32 * (1.0 - 0x1.0p-12));
-      const double hw = fmin(hi, (double)hi32 * (1.0 + 0x1.0p-12));
-      if (lw > lo || hw < hi) {
-        double fl2, fh2;
-        int el2, eh2;
-        const int cl2 = lw > lo ? sturm_eval(oo, n, lw, fl2, el2) : c_lo;
-        const int ch2 = hw < hi ? sturm_eval(oo, n, hw, fh2, eh2) : c_hi;
-        if (cl2 <= j && ch2 >= j + 1) {
-          if (lw > lo) { lo = lw; c_lo = cl2; f_lo = fl2; e_lo = el2; }
-          if (hw < hi) { hi = hw; c_hi = ch2; f_hi = fh2; e_hi = eh2; }
-        }
-      }
+    // FP64: verify the bracket widened by 2^-12 on each side (the FP32 count's
+    // error is a relative 2n 2^-23 at most); if it does not hold, start from
+    // the whole range [zero bound, |T|]
+    double lo = fmax(tlo, (double)lo32 * (1.0 - 0x1.0p-12));
+    double hi = fmin(top, (double)hi32 * (1.0 + 0x1.0p-12));
+    double f_lo, f_hi;
+    int e_lo, e_hi;
+    int c_lo = sturm_eval(oo, n, lo, f_lo, e_lo);
+    int c_hi = sturm_eval(oo, n, hi, f_hi, e_hi);
+    if (!(c_lo <= j && c_hi >= j + 1)) {
+      lo = tlo; c_lo = zlo; f_lo = s_f0; e_lo = s_e0;
+      hi = top; c_hi = sturm_eval(oo, n, hi, f_hi, e_hi);
     }
+    // FP64 refinement to 2^-51 |T|: Illinois steps while the bracket holds one
+    // value, bisection otherwise
     int last = 0, run = 0;
     for (int it = 0; it < 80 && hi - lo > tol; ++it) {
-      const bool interp = have_lo && c_lo == j && c_hi == j + 1 && run < 3;
+      const bool interp = c_lo == j && c_hi == j + 1 && run < 3;
       // a bracket spanning more than a factor 2 is split geometrically (the
       // spectrum decays over many decades), a narrower one in the middle
       double x = (lo > 0.0 && hi > 2.0 * lo) ? sqrt(lo * hi) : 0.5 * (lo + hi);
@@ -525,7 +519,7 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
         run = (last == 1) ? run + 1 : 1;
         last = 1;
       } else {
-        lo = x; c_lo = c; f_lo = f; e_lo = fe; have_lo = true;
+        lo = x; c_lo = c; f_lo = f; e_lo = fe;
         if (interp && last == -1) e_hi -= 1;
         run = (last == -1) ? run + 1 : 1;
         last = -1;
@@ -783,7 +777,7 @@ cudaError_t launch_bidiag(const BidiagArgs& a, cudaStream_t st) {
 cudaError_t launch_bd_bisect(const double* bd, int n, int n_pad, int S, double* sig, int* perm, int* nnz,
                              double* lns1, double zero_rel, cudaStream_t st) {
   if (S <= 0) return cudaSuccess;
-  const size_t smem = (size_t)2 * n * (sizeof(double) + sizeof(float)) + kBisThreads * (sizeof(double) + 2 * sizeof(int));
+  const size_t smem = (size_t)2 * n * (sizeof(double) + sizeof(float)) + kBisThreads * sizeof(int);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
