@@ -34,7 +34,24 @@ namespace mctrg {
 
 namespace {
 constexpr int kThreads = 128;
-constexpr int kVch = 8;     // kept vectors staged per pass of the M v product
+constexpr int kVch = 16;    // kept vectors staged per pass of the M v product
+
+// Sum of 16 per-lane values over the warp, all at once: four halving exchanges
+// (each lane keeps the half of its values its partner does not) and a last
+// butterfly; on return lane l holds the total of value (l >> 1).
+__device__ __forceinline__ double warp_sum16(double (&v)[16], int lane) {
+#pragma unroll
+  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool hi = lane & o;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const double keep = hi ? v[j + h] : v[j];
+      const double send = hi ? v[j] : v[j + h];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -249,16 +266,12 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
             for (int q = 0; q < kVch; ++q)
               if (q < nv) acc[q] = fma(mv, vbuf[q * n + col], acc[q]);
           }
-#pragma unroll
-          for (int q = 0; q < kVch; ++q) {
-            if (q < nv) {
-              const double s = warp_sum(acc[q]);
-              if (lane == 0) {
-                const int r = s_kept[a0 + q];
-                const double sr = sg[r];
-                Hl[(size_t)row * kc + a0 + q] = sqrt(s_sigt[a0 + q]) * s / (sr * sr);
-              }
-            }
+          const double sum = warp_sum16(acc, lane);
+          const int q = lane >> 1;
+          if (!(lane & 1) && q < nv) {
+            const int r = s_kept[a0 + q];
+            const double sr = sg[r];
+            Hl[(size_t)row * kc + a0 + q] = sqrt(s_sigt[a0 + q]) * sum / (sr * sr);
           }
         }
       }
