@@ -100,3 +100,15 @@ def test_merge_matches_oracle_on_whole_sample():
 def test_merge_rejects_empty():
     with pytest.raises(mctrg.MctrgError):
         mctrg.mctrg_merge_estimates([mctrg.Estimate()])
+
+
+def test_create_rejects_bad_options_before_touching_the_device():
+    # option checks come first, so they hold on a host without a GPU
+    import ctypes
+    lib = mctrg.lib()
+    h = ctypes.c_void_p()
+    for bad in (dict(precision=9), dict(svd=3), dict(svd=-1), dict(zero_tol_scale=-1.0),
+                dict(zero_tol_scale=float("inf")), dict(zero_tol_scale=float("nan"))):
+        o = mctrg.make_options(**bad)
+        assert lib.mctrg_create(ctypes.byref(o), ctypes.byref(h)) == mctrg.MCTRG_EINVAL, bad
+    assert lib.mctrg_create(None, ctypes.byref(h)) == mctrg.MCTRG_EINVAL
