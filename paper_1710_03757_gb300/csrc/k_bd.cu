@@ -41,6 +41,7 @@ namespace {
 constexpr int kBdThreads = 256;
 constexpr int kBisThreads = 256;
 constexpr int kInvitIters = 3;
+constexpr int kCh = 8;          // steps per block of the inverse iteration's serial loops
 constexpr double kEps = 0x1.0p-52;
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -587,42 +588,73 @@ __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a, int ls) {
     double rs = 1.0;                                 // scale owed by the stored iterate
     for (int iter = 0; iter < kInvitIters; ++iter) {
       if (on) {
+        // factor T - s I = P L U, applying L^-1 P^T to the right-hand side as it
+        // goes; the loads of each block of kCh steps are issued together, so the
+        // serial chain waits on memory once per block instead of once per step
         double dg = -sgm, du = OFFD(0), xi = XB(0) * rs;
-        for (int i = 0; i < m - 1; ++i) {
-          const double dli = OFFD(i);
-          const double dun = (i + 1 < m - 1) ? OFFD(i + 1) : 0.0;
-          const double xn = XB(i + 1) * rs;
-          if (fabs(dg) >= fabs(dli)) {
-            const double g = (dg == 0.0) ? kEps : dg;
-            const double f = dli / g;
-            DG(i) = g; DU(i) = du; DU2(i) = 0.0; XB(i) = xi;
-            dg = -sgm - f * du;
-            du = dun;
-            xi = xn - f * xi;
-          } else {
-            const double f = dg / dli;
-            DG(i) = dli; DU(i) = -sgm; DU2(i) = dun; XB(i) = xn;
-            dg = du + f * sgm;
-            du = -f * dun;
-            xi = xi - f * xn;
+        for (int base = 0; base < m - 1; base += kCh) {
+          double xnb[kCh], odb[kCh + 1];
+#pragma unroll
+          for (int c = 0; c < kCh; ++c) {
+            const int i = base + c;
+            xnb[c] = (i + 1 < m) ? XB(i + 1) : 0.0;
+            odb[c] = (i < m - 1) ? OFFD(i) : 0.0;
+          }
+          odb[kCh] = (base + kCh < m - 1) ? OFFD(base + kCh) : 0.0;
+#pragma unroll
+          for (int c = 0; c < kCh; ++c) {
+            const int i = base + c;
+            if (i >= m - 1) break;
+            const double dli = odb[c];                 // sub-diagonal = off-diagonal
+            const double dun = (i + 1 < m - 1) ? odb[c + 1] : 0.0;
+            const double xn = xnb[c] * rs;
+            if (fabs(dg) >= fabs(dli)) {
+              const double g = (dg == 0.0) ? kEps : dg;
+              const double f = dli / g;
+              DG(i) = g; DU(i) = du; DU2(i) = 0.0; XB(i) = xi;
+              dg = -sgm - f * du;
+              du = dun;
+              xi = xn - f * xi;
+            } else {
+              const double f = dg / dli;
+              DG(i) = dli; DU(i) = -sgm; DU2(i) = dun; XB(i) = xn;
+              dg = du + f * sgm;
+              du = -f * dun;
+              xi = xi - f * xn;
+            }
           }
         }
-        DG(m - 1) = (dg == 0.0) ? kEps : dg;
-        // back substitution U x = y, carrying x_{i+1}, x_{i+2}
-        double x1 = xi / DG(m - 1);
+        const double glast = (dg == 0.0) ? kEps : dg;
+        DG(m - 1) = glast;
+        // back substitution U x = y, carrying x_{i+1}, x_{i+2}, in blocks of kCh
+        double x1 = xi / glast;
         XB(m - 1) = x1;
         double s2 = x1 * x1;
         double x2 = 0.0;
-        for (int i = m - 2; i >= 0; --i) {
-          double x = (XB(i) - DU(i) * x1 - DU2(i) * x2) / DG(i);
-          if (exp_field(x) > 1023 + 600) {           // growth through tiny pivots: rescale x[i..]
-            for (int q = i + 1; q < m; ++q) XB(q) *= 0x1.0p-600;
-            x *= 0x1.0p-600; x1 *= 0x1.0p-600; x2 *= 0x1.0p-600; s2 *= 0x1.0p-1200;
+        for (int top = m - 2; top >= 0; top -= kCh) {
+          double yb[kCh], ub[kCh], u2b[kCh], gb[kCh];
+#pragma unroll
+          for (int c = 0; c < kCh; ++c) {
+            const int i = top - c;
+            yb[c] = i >= 0 ? XB(i) : 0.0;
+            ub[c] = i >= 0 ? DU(i) : 0.0;
+            u2b[c] = i >= 0 ? DU2(i) : 0.0;
+            gb[c] = i >= 0 ? DG(i) : 1.0;
           }
-          XB(i) = x;
-          s2 = fma(x, x, s2);
-          x2 = x1;
-          x1 = x;
+#pragma unroll
+          for (int c = 0; c < kCh; ++c) {
+            const int i = top - c;
+            if (i < 0) break;
+            double x = (yb[c] - ub[c] * x1 - u2b[c] * x2) / gb[c];
+            if (exp_field(x) > 1023 + 600) {         // growth through tiny pivots: rescale x[i..]
+              for (int q = i + 1; q < m; ++q) XB(q) *= 0x1.0p-600;
+              x *= 0x1.0p-600; x1 *= 0x1.0p-600; x2 *= 0x1.0p-600; s2 *= 0x1.0p-1200;
+            }
+            XB(i) = x;
+            s2 = fma(x, x, s2);
+            x2 = x1;
+            x1 = x;
+          }
         }
         rs = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
         if (clustered) {                             // unit iterates for the Gram-Schmidt below
