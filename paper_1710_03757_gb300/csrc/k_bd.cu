@@ -77,8 +77,10 @@ __device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >
 //    A[k][j] - w_j, from which the right reflector G = I - tauR u u^T,
 //    u = (1, r_{k+2..}/(r_{k+1} - betaR)), is formed; then one fused pass per
 //    row i > k applies both: a = A[i][:] - v_i w, y = tauR a.u, a -= y u, and
-//    hands column k+1 of the result to step k+1.  The trailing matrix is read
-//    twice and written once per step (the column dots w, the fused pass).
+//    hands column k+1 of the result to step k+1 together with step k+1's
+//    column dots (w is linear in the unnormalized column, so the fused pass
+//    accumulates sum_i A'[i][k+1] A'[i][:] from the rows it holds).  The
+//    trailing matrix is read and written once per step.
 //    Lane l holds the trailing columns k+1+l, k+1+l+32, ... of a row in
 //    registers; the number of live 32-column chunks, QL, is a template
 //    argument chosen per step, so no FMA is issued for a finished column.  A
@@ -135,7 +137,7 @@ __device__ __forceinline__ void bd_w_pass(const BdStep& s) {
 // the R rows together; returns this lane's share of the new column k+1 squared.
 template <int QL, int R>
 __device__ __forceinline__ double bd_rows(const BdStep& s, int i0, const double (&wr)[QL], const double (&ur)[QL],
-                                          double* vcol_out) {
+                                          double (&acc)[QL], double* vcol_out) {
   const int n = s.n, k = s.k, lane = s.lane, c0 = k + 1 + lane;
   double av[R][QL];
   double y[4] = {0.0, 0.0, 0.0, 0.0};
@@ -166,19 +168,28 @@ __device__ __forceinline__ double bd_rows(const BdStep& s, int i0, const double 
       if (c0 + 32 * q < n) {
         const double v = fma(-yr[r], ur[q], av[r][q]);
         row[c0 + 32 * q] = v;
+        av[r][q] = v;
         if (q == 0 && lane == 0) {
           vcol_out[i] = v;                       // column k+1 for the next step
           if (i > k + 1) nsq = fma(v, v, nsq);
         }
       }
     }
+    // the next step's column dots: sum_{i > k+1} A'[i][k+1] A'[i][c], c > k+1
+    const double xk1 = __shfl_sync(0xffffffffu, av[r][0], 0);
+    if (i > k + 1) {
+#pragma unroll
+      for (int q = 0; q < QL; ++q)
+        if (c0 + 32 * q < n && (q > 0 || lane > 0)) acc[q] = fma(xk1, av[r][q], acc[q]);
+    }
   }
   return nsq;
 }
 
 // fused pass: rows i > k, RPW per warp (full groups), then the leftover rows of
-// the last group one at a time; returns this warp's sum of the new column k+1
-// squared below the diagonal (valid in lane 0).
+// the last group one at a time; leaves this warp's share of the next step's
+// column dots in wpart and returns its sum of the new column k+1 squared below
+// the diagonal (valid in lane 0).
 template <int QL>
 __device__ __forceinline__ double bd_fused_pass(const BdStep& s, double* vcol_out) {
   constexpr int NW = kBdThreads / 32;
@@ -192,10 +203,16 @@ __device__ __forceinline__ double bd_fused_pass(const BdStep& s, double* vcol_ou
     ur[q] = in ? s.uv[c0 + 32 * q] : 0.0;
   }
   double nsq = 0.0;
+  double acc[QL];
+#pragma unroll
+  for (int q = 0; q < QL; ++q) acc[q] = 0.0;
   int i0 = k + 1 + RPW * s.warp;
-  for (; i0 + RPW <= n; i0 += RPW * NW) nsq += bd_rows<QL, RPW>(s, i0, wr, ur, vcol_out);
+  for (; i0 + RPW <= n; i0 += RPW * NW) nsq += bd_rows<QL, RPW>(s, i0, wr, ur, acc, vcol_out);
   if (RPW > 1)
-    for (int i = i0; i < n && i < i0 + RPW; ++i) nsq += bd_rows<QL, 1>(s, i, wr, ur, vcol_out);
+    for (int i = i0; i < n && i < i0 + RPW; ++i) nsq += bd_rows<QL, 1>(s, i, wr, ur, acc, vcol_out);
+#pragma unroll
+  for (int q = 0; q < QL; ++q)
+    if (c0 + 32 * q < n && c0 + 32 * q > k + 1) s.wpart[s.warp * n + c0 + 32 * q] = acc[q];
   return nsq;
 }
 
@@ -247,30 +264,33 @@ __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_sme
   }
   __syncthreads();
   BdStep st{A, vcol, wv, uv, wpart, n, 0, lane, warp};
+  // the column dots of step 0 with the unnormalized column 0: later steps get
+  // theirs from the previous fused pass (w is linear in the column)
+  if (n > 1) BdDispatch<1, NQ>::w_pass((n - 1 + 31) >> 5, st);
+  __syncthreads();
   for (int k = 0; k < n; ++k) {
     st.k = k;
     const int ql = (n - k - 1 + 31) >> 5;     // live 32-column chunks right of column k
     // ---- left reflector from column k
     const double xn2 = s_xn2;
     const double alpha = vcol[k];
-    double tau = 0.0, beta = alpha;
+    double tau = 0.0, beta = alpha, scal = 0.0;
     if (xn2 > 0.0) {
       beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
       tau = (beta - alpha) / beta;
-      const double scal = 1.0 / (alpha - beta);
+      scal = 1.0 / (alpha - beta);
       for (int i = k + 1 + tid; i < n; i += kBdThreads) vcol[i] *= scal;
     }
     if (tid == 0) bd[k] = beta;
     if (k == n - 1) break;
     __syncthreads();
-    // ---- w = tau (A[k][:] + v^T A[k+1:, :]) on columns > k
+    // ---- w = tau (A[k][:] + v^T A[k+1:, :]) on columns > k; wpart holds
+    //      sum_{i>k} x_i A[i][:] for the unnormalized column x (v = scal x)
     if (tau != 0.0) {
-      BdDispatch<1, NQ>::w_pass(ql, st);
-      __syncthreads();
       for (int jj = k + 1 + tid; jj < n; jj += kBdThreads) {
-        double sum = A[(size_t)k * n + jj];
+        double sum = 0.0;
         for (int w = 0; w < NW; ++w) sum += wpart[w * n + jj];
-        wv[jj] = tau * sum;
+        wv[jj] = tau * fma(scal, sum, A[(size_t)k * n + jj]);
       }
     } else {
       for (int jj = k + 1 + tid; jj < n; jj += kBdThreads) wv[jj] = 0.0;
