@@ -189,7 +189,8 @@ int mctrg_merge_estimates(const mctrg_estimate* parts, int k, mctrg_estimate* ou
  *   SAMPLE   4 n kc + 2 n^2 kc per tensor (tables and draws; left halves M v)
  *   TRACE    2 D^2 d^2 per trajectory
  *   BIDIAG   (8/3) n^3 per matrix (Householder bidiagonalization)
- *   BISECT   4 n per Sturm count, 1 + 44 nnz counts per matrix
+ *   BISECT   no flop count is recorded: each nonzero value takes ~20 FP32 and
+ *            ~6 FP64 Sturm counts of 2n steps (2 FP64 operations per step)
  *   VECTORS  2 n^2 kc + 20 (2n) kc per matrix (back-transformation and
  *            inverse iteration of the kept vectors)
  * bytes_alg counts each kernel's compulsory global-memory traffic

@@ -16,7 +16,9 @@
 //                     against underflow; it is the exact count of a matrix
 //                     within a few ulps of T entrywise, so each value carries
 //                     an absolute error of a few eps |B|, the accuracy class
-//                     of LAPACK's SVD.
+//                     of LAPACK's SVD.  FP32 counts narrow each bracket (their
+//                     rounding is relative too), FP64 counts verify it, and
+//                     Illinois steps on det(T - x I) finish isolated values.
 //  (the sampler then chooses the kept indices)
 //  3. k_bd_invit      right singular vectors of B for the kept indices: inverse
 //                     iteration on T - s I (LU with partial pivoting) whose
