@@ -149,11 +149,10 @@ __device__ __forceinline__ double bd_rows(const BdStep& s, int i0, const double 
     const double* row = s.A + (size_t)(i0 + r) * n;
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
-      av[r][q] = 0.0;
-      if (c0 + 32 * q < n) {
-        av[r][q] = fma(-vi, wr[q], row[c0 + 32 * q]);
-        y[r] = fma(av[r][q], ur[q], y[r]);
-      }
+      // columns past the edge load the last column and carry zero multipliers
+      // (wr = ur = 0 there), so every FMA is issued unconditionally
+      av[r][q] = fma(-vi, wr[q], row[min(c0 + 32 * q, n - 1)]);
+      y[r] = fma(av[r][q], ur[q], y[r]);
     }
   }
   const double t = reduce4(y[0], y[1], y[2], y[3], lane);
@@ -167,23 +166,20 @@ __device__ __forceinline__ double bd_rows(const BdStep& s, int i0, const double 
     double* row = s.A + (size_t)i * n;
 #pragma unroll
     for (int q = 0; q < QL; ++q) {
-      if (c0 + 32 * q < n) {
-        const double v = fma(-yr[r], ur[q], av[r][q]);
-        row[c0 + 32 * q] = v;
-        av[r][q] = v;
-        if (q == 0 && lane == 0) {
-          vcol_out[i] = v;                       // column k+1 for the next step
-          if (i > k + 1) nsq = fma(v, v, nsq);
-        }
-      }
+      const double v = fma(-yr[r], ur[q], av[r][q]);
+      av[r][q] = v;
+      if (c0 + 32 * q < n) row[c0 + 32 * q] = v;
+    }
+    if (lane == 0) {
+      vcol_out[i] = av[r][0];                    // column k+1 for the next step
+      if (i > k + 1) nsq = fma(av[r][0], av[r][0], nsq);
     }
     // the next step's column dots: sum_{i > k+1} A'[i][k+1] A'[i][c], c > k+1
+    // (edge lanes accumulate values that are never written out)
     const double xk1 = __shfl_sync(0xffffffffu, av[r][0], 0);
-    if (i > k + 1) {
+    const double xm = i > k + 1 ? xk1 : 0.0;
 #pragma unroll
-      for (int q = 0; q < QL; ++q)
-        if (c0 + 32 * q < n && (q > 0 || lane > 0)) acc[q] = fma(xk1, av[r][q], acc[q]);
-    }
+    for (int q = 0; q < QL; ++q) acc[q] = fma(xm, av[r][q], acc[q]);
   }
   return nsq;
 }
