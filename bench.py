@@ -39,8 +39,8 @@ FP64_NOMINAL_TFLOPS = 1.25
 # summarized in profiles/k_jacobi_warp_n256_ising_L32_chi16.md (2.66 GB for 128 matrices)
 JACOBI_DRAM_BYTES_PER_MATRIX_N256 = 2.658e9 / 128
 # DRAM bytes (read + write) of one 256 x 256 matrix in k_bidiag, from the ncu capture
-# summarized in profiles/k_bidiag_n256_ising_L32_chi16.md (841.6 MB for 128 matrices)
-BIDIAG_DRAM_BYTES_PER_MATRIX_N256 = 841.62e6 / 128
+# summarized in profiles/k_bidiag_n256_ising_L32_chi16.md (810.9 MB for 128 matrices)
+BIDIAG_DRAM_BYTES_PER_MATRIX_N256 = 810.94e6 / 128
 
 
 def measured_peaks():
