@@ -311,7 +311,7 @@ def main():
 
     import numpy as np
     import torch
-    from paper_1710_03757_gb300 import build, mctrg
+    from paper_1710_03757_gb300 import build, mctrg, replicas
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -341,7 +341,7 @@ def main():
 
     def first_of(step):
         # trajectory counters: rank r, step s covers [(s * world + r) * B, ...)
-        return (step * world + rank) * B
+        return replicas.first_trajectory(step, rank, world, B)
 
     def one_step(c, step, ln, sg, fl):
         st, est = mctrg.mctrg_run(c, B, seed, first_of(step), ln, sg, fl)
@@ -407,7 +407,9 @@ def main():
     ms_max, e2e_max = float(ms_t[0]), float(ms_t[1])
     total_traj = B * args.steps * world
     value = total_traj / (ms_max / 1000.0)
-    merged = mctrg.mctrg_merge_estimates(ests)
+    # the whole job's estimate: every rank's sufficient statistics, merged exactly
+    all_ests = replicas.gather_estimates(dist, ests, device="cuda") if dist else ests
+    merged = mctrg.mctrg_merge_estimates(all_ests)
     if rank != 0:
         mctrg.mctrg_destroy(ctx)
         if dist:
