@@ -155,3 +155,21 @@ def test_error_falls_as_inverse_sqrt_n():
     big = estimate(sign, lnabs)['se_ln_Z']
     # 16x the samples -> 4x smaller error (the small-run average scatters)
     assert np.mean(small) / big == pytest.approx(4.0, rel=0.25)
+
+
+def test_oracle_per_sample_spread_matches_table1():
+    # The paper's printed per-sample std of Z~/Z on its own lattice (Sec. IV,
+    # Table 1, first row: chi~ = 6, T = 1.5, 128 spins).  A sampler drawing from
+    # a different p(e), or reweighting differently, gives a different spread.
+    # 4000 fixed-seed trajectories; the band covers the std estimate's sampling
+    # spread for this multimodal distribution (Fig. 2)
+    import os
+    from oracle.trg import Problem, run_many
+    rows = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden",
+                                                    "table1_per_sample_std.txt")) if l.strip() and l[0] != "#"]
+    chi, T, std_paper = int(rows[0][0]), float(rows[0][1]), float(rows[0][2])
+    beta = 1.0 / T
+    sign, lnabs, _ = run_many(Problem(ising.bond_spin_tensor(beta), 8, chi), 0x7AB1E, 0, 4000, workers=8)
+    z = sign * np.exp(lnabs - ising.bond_spin_transfer_lnZ(8, beta))
+    assert abs(z.mean() - 1.0) <= 4 * z.std(ddof=1) / math.sqrt(len(z))
+    assert 0.75 * std_paper <= z.std(ddof=1) <= 1.25 * std_paper
