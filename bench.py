@@ -32,14 +32,14 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "ising-L1024-chi16-fp64"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# FP64 peak of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz = 1.26
-# TFLOP/s (nominal 1.25); a DFMA throughput probe on this machine measured 1.01.
+# FP64 rate of GB300 from its unit counts: 152 SMs x 2 FP64 FMA per clock x 2
+# flops x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25).  The roofline uses the
+# library's DFMA probe measured in the same run; this is the fallback.
 FP64_NOMINAL_TFLOPS = 1.25
-# DRAM bytes (read + write) of one 256 x 256 matrix in k_jacobi_warp, from the ncu capture
-# summarized in profiles/k_jacobi_warp_n256_ising_L32_chi16.md (2.66 GB for 128 matrices)
+# DRAM bytes (read + write) of one 256 x 256 matrix, from ncu captures of the
+# kernels on a case of 128 such matrices (Ising 32 x 32, chi = 16):
+# k_jacobi_warp 2.66 GB and k_bidiag 810.9 MB per launch of 128.
 JACOBI_DRAM_BYTES_PER_MATRIX_N256 = 2.658e9 / 128
-# DRAM bytes (read + write) of one 256 x 256 matrix in k_bidiag, from the ncu capture
-# summarized in profiles/k_bidiag_n256_ising_L32_chi16.md (810.9 MB for 128 matrices)
 BIDIAG_DRAM_BYTES_PER_MATRIX_N256 = 810.94e6 / 128
 
 
@@ -327,6 +327,11 @@ def main():
         return
     if dist:
         dist.barrier()
+    # the FP64 roofline's denominator, measured on this device now (DFMA probe)
+    with ClockSampler(local) as pclk:
+        pst, fp64_peak, fp64_ms = mctrg.mctrg_measure_fp64_peak(local)
+    fp64_probe = ({"tflops": fp64_peak, "launch_ms": fp64_ms, "clocks": pclk.summary()} if pst == 0
+                  else {"error": mctrg.mctrg_strerror(pst)})
     stream = torch.cuda.Stream()
     B = wl["traj_per_step"]
     seed = 0x4D435452 + 2
@@ -423,13 +428,15 @@ def main():
                     mctrg.K_GEMM, mctrg.K_TRACE)
     if dom in flop_classes and ds.flops_alg > 0 and wl["precision"] == 0:
         achieved = ds.flops_alg / (ds.ms / 1000.0) / 1e12 if ds.ms > 0 else 0.0
-        peak = FP64_NOMINAL_TFLOPS
+        peak = fp64_peak if pst == 0 and fp64_peak > 0 else FP64_NOMINAL_TFLOPS
         per_matrix = {mctrg.K_JACOBI: JACOBI_DRAM_BYTES_PER_MATRIX_N256,
                       mctrg.K_BIDIAG: BIDIAG_DRAM_BYTES_PER_MATRIX_N256}.get(dom)
         roof = {"bound": "alu", "kernel": mctrg.KERNEL_NAMES[dom], "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": "nominal FP64 (DFMA) rate of GB300, 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz; "
-                               "the FP64 GEMM of this workload runs at 1.25 TFLOP/s",
+                "peak_source": ("measured: the library's DFMA throughput probe (mctrg_measure_fp64_peak) "
+                                "in this run" if pst == 0 else
+                                "nominal FP64 rate of GB300 from unit counts (probe failed)"),
+                "peak_nominal": FP64_NOMINAL_TFLOPS, "fp64_probe": fp64_probe,
                 "traffic": (per_matrix * ds.items / max(1, ds.launches)
                             if per_matrix and wl["chi"] == 16 else None),
                 "traffic_note": "bytes per launch, scaled from the per-matrix DRAM bytes of the ncu capture",

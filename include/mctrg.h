@@ -244,7 +244,10 @@ int mctrg_svd_batched(const double* M, int n, int64_t batch, double* sigma, doub
  * reuses the same array and its flag word is cleared at the start of each
  * call; two calls whose work overlapped on the device would race, so calls
  * from one process are serialized and each returns only after `stream` has
- * completed.  `stream` must belong to the current device.
+ * completed, also when it fails after queueing work.  The array and that
+ * serialization are per process and per device: another process (or another
+ * loaded copy of the library) has its own array and is not serialized
+ * against this one.  `stream` must belong to the current device.
  * Errors: EINVAL, ECUDA, ENOCONV. */
 #define MCTRG_SVD_NOALLOC_MAX_N 1024
 int mctrg_svd_batched_noalloc(const double* M, int n, int64_t batch, double* sigma, double* vt,
@@ -266,6 +269,17 @@ int mctrg_svd_batched_noalloc(const double* M, int n, int64_t batch, double* sig
  * 2 <= n <= 1024, 0 <= n_vec <= min(32, n).  Errors: EINVAL, ENOMEM, ECUDA. */
 int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, double* sigma, int n_vec,
                              double* vt, void* stream);
+
+/* ---- measurement ------------------------------------------------------ *
+ * FP64 arithmetic rate of a device, the peak against which the FP64 kernels
+ * (the SVD routes, the FP64 contraction) are quoted: a probe kernel runs, in
+ * every thread of a whole number of CTAs per SM, 8 independent chains of
+ * `steps` fused multiply-adds (x <- x b + c); one untimed launch, then the
+ * best of three launches timed with CUDA events on the legacy default
+ * stream.  *tflops = 16 steps threads / time; *ms (may be NULL) receives the
+ * best launch's duration.  The paper has no counterpart (it reports no
+ * timings).  steps >= 4, a multiple of 4.  Errors: EINVAL, ECUDA. */
+int mctrg_measure_fp64_peak(int device, int64_t steps, double* tflops, double* ms);
 
 /* Release every resource of the context (NULL is a no-op). */
 void mctrg_destroy(mctrg_ctx_t ctx);

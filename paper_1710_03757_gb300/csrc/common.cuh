@@ -1,6 +1,7 @@
 // Shared device/host helpers of the MC-TRG library: TRG geometry on the
 // torus, the Philox4x32-10 uniform stream, and error plumbing.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -110,5 +111,21 @@ MCTRG_HD double philox_uniform(uint64_t seed, uint32_t traj, uint32_t level,
 constexpr uint32_t FLAG_SPLIT_CLUSTER = 1u, FLAG_DRAW_TIE = 2u, FLAG_TINY_KEPT = 4u,
                    FLAG_NOCONV = 16u;
 constexpr double GAP_TOL = 1e-8, TIE_TOL = 1e-9, TINY_TOL = 1e-7;
+
+// Raise a kernel's dynamic shared-memory limit on the current device, once
+// per (kernel, device); safe to call from several host threads at once (a
+// race only repeats the call).  `done` holds one bit per device ordinal
+// below 64; higher ordinals set the attribute on every call.
+template <class Kernel>
+inline cudaError_t raise_smem_limit(Kernel* kernel, int bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 }  // namespace mctrg

@@ -804,11 +804,9 @@ static cudaError_t launch_bidiag_nq(const BidiagArgs& a, cudaStream_t st) {
   // rows in the global workspace: ask for enough shared memory that one CTA
   // runs per SM, so the resident matrices stay in L2
   const size_t smem = use_smem ? rows + aux : std::max<size_t>(aux, 120 * 1024);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_bidiag<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 1024);
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t e = raise_smem_limit(k_bidiag<NQ>, 200 * 1024 + 1024, attr);
+  if (e != cudaSuccess) return e;
   k_bidiag<NQ><<<a.S, kBdThreads, smem, st>>>(a, use_smem);
   return cudaGetLastError();
 }
@@ -829,11 +827,9 @@ cudaError_t launch_bd_bisect(const double* bd, int n, int n_pad, int S, double* 
   if (S <= 0) return cudaSuccess;
   const size_t smem = (size_t)2 * n * (sizeof(double) + sizeof(float)) + kBisThreads * sizeof(int);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_bd_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t e = raise_smem_limit(k_bd_bisect, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
   k_bd_bisect<<<S, kBisThreads, smem, st>>>(bd, n, n_pad, sig, perm, nnz, lns1, zero_rel);
   return cudaGetLastError();
 }
@@ -858,11 +854,9 @@ cudaError_t launch_bd_vectors(const BdVecArgs& a, cudaStream_t st) {
   k_bd_invit<<<invit_slots(a.n, a.S), 32, 0, st>>>(a, a.kmax <= 16 ? 16 : 32);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_bd_backtr, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  e = raise_smem_limit(k_bd_backtr, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)a.S, (unsigned)((std::max(1, a.kmax) + kBtGroup - 1) / kBtGroup));
   k_bd_backtr<<<grid, 128, smem, st>>>(a);
   return cudaGetLastError();

@@ -287,11 +287,9 @@ cudaError_t launch_sample_split(const SampleArgs& a, cudaStream_t st, int grid) 
   if (a.chi > 32 || a.kc > 32) return cudaErrorInvalidValue;
   const size_t smem = (size_t)a.n_pad * 2 * sizeof(double) + (size_t)kVch * a.n * sizeof(double) +
                       (size_t)a.n_pad + 16;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_sample_split, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t e = raise_smem_limit(k_sample_split, 160 * 1024, attr);
+  if (e != cudaSuccess) return e;
   if (grid > a.n_items) grid = (int)a.n_items;
   k_sample_split<<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();

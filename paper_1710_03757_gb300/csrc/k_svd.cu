@@ -547,11 +547,9 @@ static cudaError_t launch_warp_variant(const JacobiArgs& a, int threads, cudaStr
   // CTA runs per SM, so the rows of the resident matrices stay in L2.
   const size_t staging = (size_t)(threads / 32) * n * sizeof(double);
   const size_t smem = use_smem ? rows_bytes + aux : std::max<size_t>(aux + staging, 120 * 1024);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_jacobi_warp<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 64);
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t e = raise_smem_limit(k_jacobi_warp<PW>, 200 * 1024 + 64, attr);
+  if (e != cudaSuccess) return e;
   k_jacobi_warp<PW><<<a.S, threads, smem, st>>>(a, use_smem);
   return cudaGetLastError();
 }
@@ -590,11 +588,9 @@ cudaError_t launch_jacobi(const JacobiArgs& a, cudaStream_t st) {
   if (G > 2 && G >= n) G >>= 1;                 // about two elements per lane
   int threads = n <= 16 ? 32 : (n <= 64 ? 256 : 512);
   if (threads < G) threads = G;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 64);
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t e = raise_smem_limit(k_jacobi, 200 * 1024 + 64, attr);
+  if (e != cudaSuccess) return e;
   k_jacobi<<<a.S, threads, smem, st>>>(a, use_smem, G);
   return cudaGetLastError();
 }

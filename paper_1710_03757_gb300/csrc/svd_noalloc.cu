@@ -29,7 +29,10 @@ constexpr size_t kScratchDoubles = kScratchBytes / sizeof(double);
 static __device__ __align__(256) double g_svd_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 256;
-std::mutex g_lock;                         // one call at a time per process
+// One call at a time per process.  The array and this lock belong to one
+// process (and one loaded copy of the library): calls from other processes
+// have arrays of their own and are not serialized against these.
+std::mutex g_lock;
 double* g_scratch_addr[kMaxDevices] = {};  // device address of the array, per device
 
 // The array's name is only a host-side stand-in; its device address is
@@ -54,6 +57,13 @@ __global__ void k_or_flags(const uint32_t* f, int64_t n) {
 }
 
 __global__ void k_clear_flag_word() { ((unsigned int*)&g_svd_scratch[0])[0] = 0u; }
+
+// Wait for the work already queued on `st` before the caller releases the
+// lock; returns `status` (the wait's own failure leaves nothing more to do).
+int drain(cudaStream_t st, int status) {
+  cudaStreamSynchronize(st);
+  return status;
+}
 
 }  // namespace
 
@@ -81,20 +91,22 @@ extern "C" int mctrg_svd_batched_noalloc(const double* M, int n, int64_t batch, 
   int* nnz = perm + (size_t)C * np;
   uint32_t* flags = (uint32_t*)(nnz + C);
   k_clear_flag_word<<<1, 1, 0, st>>>();
-  if (cudaGetLastError() != cudaSuccess) return MCTRG_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return drain(st, MCTRG_ECUDA);
   for (int64_t b0 = 0; b0 < batch; b0 += C) {
     const int64_t cnt = (C < batch - b0) ? C : batch - b0;
-    if (cudaMemsetAsync(flags, 0, sizeof(uint32_t) * cnt, st) != cudaSuccess) return MCTRG_ECUDA;
+    // an error after work was queued returns only once that work has left
+    // the shared array (drain), so the next call cannot race with it
+    if (cudaMemsetAsync(flags, 0, sizeof(uint32_t) * cnt, st) != cudaSuccess) return drain(st, MCTRG_ECUDA);
     if (mctrg::svd_chunk(M + (size_t)b0 * n * n, n, cnt, sigma + (size_t)b0 * n,
                          vt ? vt + (size_t)b0 * n * n : nullptr, max_sweeps, W, sig, perm, nnz, flags,
                          st) != cudaSuccess)
-      return MCTRG_ECUDA;
+      return drain(st, MCTRG_ECUDA);
     k_or_flags<<<1, 256, 0, st>>>(flags, cnt);
-    if (cudaGetLastError() != cudaSuccess) return MCTRG_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return drain(st, MCTRG_ECUDA);
   }
   unsigned int word = 0;
-  if (cudaMemcpyAsync(&word, base, sizeof(word), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return MCTRG_ECUDA;
+  if (cudaMemcpyAsync(&word, base, sizeof(word), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return drain(st, MCTRG_ECUDA);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MCTRG_ECUDA;
   return (word & mctrg::FLAG_NOCONV) ? MCTRG_ENOCONV : MCTRG_OK;
 }

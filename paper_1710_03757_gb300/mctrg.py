@@ -23,7 +23,7 @@ EXPORTS = [
     "mctrg_server_create", "mctrg_server_submit", "mctrg_server_poll", "mctrg_server_wait",
     "mctrg_server_destroy", "mctrg_plan_level", "mctrg_philox_uniform", "mctrg_kernel_stats",
     "mctrg_reset_kernel_stats", "mctrg_svd_batched", "mctrg_svd_batched_noalloc",
-    "mctrg_svd_bidiag_batched",
+    "mctrg_svd_bidiag_batched", "mctrg_measure_fp64_peak",
 ]
 K_FORM_XY, K_GEMM, K_JACOBI, K_SAMPLE, K_TRACE, K_OTHER, K_BIDIAG, K_BISECT, K_VECTORS, K_COUNT = range(10)
 KERNEL_NAMES = ["form_xy", "gemm", "jacobi", "sample_split", "trace", "other", "bidiag", "bisect", "vectors"]
@@ -91,6 +91,7 @@ def lib():
             "mctrg_svd_batched": (c_int, [vp, c_int, i64, vp, vp, c_int, vp]),
             "mctrg_svd_batched_noalloc": (c_int, [vp, c_int, i64, vp, vp, c_int, vp]),
             "mctrg_svd_bidiag_batched": (c_int, [vp, c_int, i64, vp, c_int, vp, vp]),
+            "mctrg_measure_fp64_peak": (c_int, [c_int, i64, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -221,6 +222,13 @@ def mctrg_svd_bidiag_batched(M, sigma, vt=None, stream=None):
     batch, n = int(M.shape[0]), int(M.shape[-1])
     nv = 0 if vt is None else int(vt.shape[1])
     return lib().mctrg_svd_bidiag_batched(_ptr(M), n, batch, _ptr(sigma), nv, _ptr(vt), stream)
+
+
+def mctrg_measure_fp64_peak(device=0, steps=1 << 16):
+    """(status, TFLOP/s, ms) of the library's DFMA throughput probe."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    s = lib().mctrg_measure_fp64_peak(int(device), int(steps), ctypes.byref(tf), ctypes.byref(ms))
+    return s, tf.value, ms.value
 
 
 def mctrg_destroy(ctx):

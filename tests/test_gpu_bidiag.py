@@ -15,7 +15,8 @@ from oracle.trg import Problem, run_many
 from paper_1710_03757_gb300 import build, mctrg
 from paper_1710_03757_gb300.workloads import generic_tensor, seed_for
 
-from test_gpu_parity import compare, gpu_run
+from parity import compare
+from test_gpu_parity import gpu_run
 
 pytestmark = pytest.mark.gpu
 
@@ -118,7 +119,7 @@ def test_generic_tensor_parity_bidiag(torch, L, chi, D, n):
     seed = 0xC0FFEE + L + chi
     gpu = gpu_run(L, chi, n, seed, T0=T0, svd=mctrg.SVD_BIDIAG)
     orc = run_many(Problem(T0, L, chi), seed, 0, n)
-    assert compare(gpu, orc, min_ok=0.9) >= 0.9 * n
+    assert compare(gpu, orc, min_ok=0.9, label="bidiag generic L%d chi%d D%d" % (L, chi, D)) >= 0.9 * n
 
 
 @pytest.mark.parametrize("beta,h,L,chi,n", [(0.3, 0.1, 8, 4, 100), (0.44, 0.05, 8, 2, 200)])
@@ -126,7 +127,7 @@ def test_ising_parity_bidiag(torch, beta, h, L, chi, n):
     seed = 991 + L
     gpu = gpu_run(L, chi, n, seed, beta=beta, h=h, svd=mctrg.SVD_BIDIAG)
     orc = run_many(Problem(ising.site_tensor(beta, h), L, chi), seed, 0, n)
-    compare(gpu, orc, min_ok=0.5)
+    compare(gpu, orc, min_ok=0.5, label="bidiag ising b%g h%g L%d chi%d" % (beta, h, L, chi))
 
 
 @pytest.mark.parametrize("case", ["ising", "generic3"])
@@ -141,14 +142,14 @@ def test_chi32_parity_n1024_levels(torch, case):
         T0, L, n = generic_tensor(3, seed=9), 8, 6
         gpu = gpu_run(L, 32, n, 31, T0=T0)
     orc = run_many(Problem(T0, L, 32), 31, 0, n, workers=n)
-    compare(gpu, orc, min_ok=0.5)
+    compare(gpu, orc, min_ok=0.5, label="chi32 " + case)
 
 
 def test_n64_parity_bidiag(torch):
     T0 = generic_tensor(2, seed=7)
     gpu = gpu_run(8, 8, 24, 5, T0=T0, svd=mctrg.SVD_BIDIAG)
     orc = run_many(Problem(T0, 8, 8), 5, 0, 24, workers=4)
-    compare(gpu, orc, min_ok=0.8)
+    compare(gpu, orc, min_ok=0.8, label="bidiag n64")
 
 
 @pytest.mark.parametrize("L,beta,h,n", [(16, 0.44, 0.0, 32), (32, 0.40, 0.05, 16), (64, 0.44, 0.0, 16)])
@@ -157,7 +158,7 @@ def test_ising_chi16_parity_auto_route(torch, L, beta, h, n):
     seed = seed_for(2) + L
     gpu = gpu_run(L, 16, n, seed, beta=beta, h=h)
     orc = run_many(Problem(ising.site_tensor(beta, h), L, 16), seed, 0, n, workers=8)
-    compare(gpu, orc, min_ok=0.5)
+    compare(gpu, orc, min_ok=0.5, label="auto ising chi16 L%d" % L)
 
 
 def test_routes_agree_at_L1024(torch):

@@ -1,9 +1,14 @@
 """GPU parity: the CUDA path (through the C ABI) against the oracle.
 
-Per trajectory, on trajectories neither side flags as a near-tie, the sign
-must agree and |ln|Z~|_gpu - ln|Z~|_oracle| <= 1e-10 * max(1, |ln Z|)  (FP64
-everywhere; both sides consume the same Philox stream).  Estimates must lie
-within 3 standard errors of the exact Z where one is known.
+Per trajectory (tests/parity.py): the flags agree, and on unflagged
+trajectories the sign agrees and |ln|Z~|_gpu - ln|Z~|_oracle| <= 1e-10 *
+max(1, |ln Z|)  (FP64 everywhere; both sides consume the same Philox
+stream); the device estimate equals the oracle's estimator on the GPU's own
+outputs.  Estimates must lie within 3 standard errors of the exact Z where
+one is known.
+
+The min_ok floors (fraction of unflagged trajectories a case accepts) sit
+below the flag rates measured on GB300 for the same seeds (printed with -s).
 """
 import math
 
@@ -16,8 +21,9 @@ from oracle.trg import Problem, run_many
 from paper_1710_03757_gb300 import build, mctrg
 from paper_1710_03757_gb300.workloads import generic_tensor, seed_for
 
+from parity import check_estimate, compare
+
 pytestmark = pytest.mark.gpu
-TOL = 1e-10
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -44,29 +50,21 @@ def gpu_run(L, chi, n, seed, beta=None, h=0.0, T0=None, first=0, **opts):
         mctrg.mctrg_destroy(ctx)
 
 
-def compare(gpu, orc, min_ok=0.5):
-    _, gl, gs, gf = gpu
-    os_, ol, of = orc
-    ok = (gf == 0) & (of == 0)
-    assert ok.mean() >= min_ok, "too many flagged trajectories: %d of %d" % (np.sum(~ok), len(ok))
-    np.testing.assert_array_equal(gs[ok], os_[ok])
-    nz = ok & (os_ != 0)
-    err = np.abs(gl[nz] - ol[nz]) / np.maximum(1.0, np.abs(ol[nz]))
-    assert err.max() <= TOL, "max rel err %.3e at %d" % (err.max(), np.argmax(err))
-    return int(ok.sum())
-
-
 def test_config1_parity_and_unbiased():
     # 2D Ising 4x4 periodic, h = 0, beta = 0.44, chi = 2, 1000 trajectories
     seed = seed_for(1)
     gpu = gpu_run(4, 2, 1000, seed, beta=0.44)
     orc = run_many(Problem(ising.site_tensor(0.44, 0.0), 4, 2), seed, 0, 1000)
-    compare(gpu, orc, min_ok=0.9)
+    compare(gpu, orc, min_ok=0.9, label="config1")
     est = gpu[0]
     z = math.exp(ising.brute_force_lnZ(4, 0.44) - est.ln_scale)
     assert abs(est.mean_Z_scaled - z) <= 3 * est.se_Z_scaled
+    # every negative trajectory is accounted for: the totals differ only
+    # through flagged trajectories whose signs differ (compare lists them)
     ref = estimate(orc[0], orc[1])
-    assert est.n_negative == ref['n_negative'] or abs(est.n_negative - ref['n_negative']) <= 5
+    flagged = gpu[3] != 0
+    d_flagged = int(np.sum(gpu[2][flagged] < 0)) - int(np.sum(orc[0][flagged] < 0))
+    assert est.n_negative - ref['n_negative'] == d_flagged
 
 
 @pytest.mark.parametrize("L,chi,D,n", [(4, 2, 2, 300), (4, 3, 2, 300), (8, 4, 2, 120), (4, 4, 3, 80),
@@ -76,7 +74,7 @@ def test_generic_tensor_parity(L, chi, D, n):
     seed = 0xC0FFEE + L + chi
     gpu = gpu_run(L, chi, n, seed, T0=T0)
     orc = run_many(Problem(T0, L, chi), seed, 0, n)
-    assert compare(gpu, orc, min_ok=0.9) >= 0.9 * n
+    assert compare(gpu, orc, min_ok=0.9, label="generic L%d chi%d D%d" % (L, chi, D)) >= 0.9 * n
 
 
 @pytest.mark.parametrize("beta,h,L,chi,n", [(0.3, 0.1, 8, 4, 100), (0.6, 0.0, 4, 2, 300),
@@ -85,7 +83,7 @@ def test_ising_parity(beta, h, L, chi, n):
     seed = 991 + L
     gpu = gpu_run(L, chi, n, seed, beta=beta, h=h)
     orc = run_many(Problem(ising.site_tensor(beta, h), L, chi), seed, 0, n)
-    compare(gpu, orc, min_ok=0.5)
+    compare(gpu, orc, min_ok=0.5, label="ising b%g h%g L%d chi%d" % (beta, h, L, chi))
 
 
 def test_shared_memory_jacobi_n64():
@@ -93,10 +91,10 @@ def test_shared_memory_jacobi_n64():
     T0 = generic_tensor(2, seed=7)
     gpu = gpu_run(8, 8, 24, 5, T0=T0)
     orc = run_many(Problem(T0, 8, 8), 5, 0, 24, workers=4)
-    compare(gpu, orc, min_ok=0.8)
+    compare(gpu, orc, min_ok=0.8, label="generic n64")
     gpu = gpu_run(8, 8, 24, 6, beta=0.44)
     orc = run_many(Problem(ising.site_tensor(0.44, 0.0), 8, 8), 6, 0, 24, workers=4)
-    compare(gpu, orc, min_ok=0.5)
+    compare(gpu, orc, min_ok=0.5, label="ising n64")
 
 
 def test_global_workspace_jacobi_n256():
@@ -104,7 +102,7 @@ def test_global_workspace_jacobi_n256():
     T0 = generic_tensor(2, seed=8)
     gpu = gpu_run(8, 16, 32, 12, T0=T0)
     orc = run_many(Problem(T0, 8, 16), 12, 0, 32, workers=8)
-    compare(gpu, orc, min_ok=0.7)
+    compare(gpu, orc, min_ok=0.7, label="generic n256 jacobi")
 
 
 @pytest.mark.parametrize("L,beta,h,n", [(16, 0.44, 0.0, 32), (32, 0.40, 0.05, 16)])
@@ -113,7 +111,7 @@ def test_ising_chi16_parity(L, beta, h, n):
     seed = seed_for(2) + L
     gpu = gpu_run(L, 16, n, seed, beta=beta, h=h)
     orc = run_many(Problem(ising.site_tensor(beta, h), L, 16), seed, 0, n, workers=8)
-    compare(gpu, orc, min_ok=0.5)
+    compare(gpu, orc, min_ok=0.5, label="ising chi16 L%d" % L)
 
 
 def test_full_size_L1024_properties():
@@ -138,7 +136,7 @@ def test_zero_tol_scale_parity(svd):
     seed, n, scale = 4321, 100, 1e9
     gpu = gpu_run(8, 4, n, seed, T0=T0, svd=svd, zero_tol_scale=scale)
     orc = run_many(Problem(T0, 8, 4, zero_tol_scale=scale), seed, 0, n)
-    assert compare(gpu, orc, min_ok=0.9) >= 0.9 * n
+    assert compare(gpu, orc, min_ok=0.9, label="zero_tol_scale svd%d" % svd) >= 0.9 * n
 
 
 def test_exact_path_L2():
@@ -203,5 +201,41 @@ def test_error_codes():
         assert mctrg.mctrg_run(ctx, 0, 1)[0] == mctrg.MCTRG_EINVAL
         assert mctrg.mctrg_run(ctx, 10, 1, 2 ** 32 - 5)[0] == mctrg.MCTRG_EINVAL
         assert mctrg.mctrg_footprint(ctx, 1000) > 0
+    finally:
+        mctrg.mctrg_destroy(ctx)
+
+
+@pytest.mark.parametrize("case", ["generic-negative", "ising-large-n", "chunked"])
+def test_device_estimate_equals_oracle_estimator(case):
+    # the estimator kernel's reductions (max, sum of scaled values, centered
+    # second moment, negative and flagged counts) against the oracle's
+    # estimator on the GPU's own per-trajectory outputs (Sec. III, Eq.
+    # infiniteEnsemble; Sec. V, Eq. shrunkDev)
+    if case == "generic-negative":
+        # a sign-indefinite generic tensor: some trajectories come out negative
+        T0 = generic_tensor(2, seed=3) - 1.0
+        est, ln, sg, fl = gpu_run(4, 2, 4000, 99, T0=T0)
+        assert np.sum(sg < 0) > 0
+    elif case == "ising-large-n":
+        est, ln, sg, fl = gpu_run(8, 2, 150000, 17, beta=0.5)
+    else:
+        est, ln, sg, fl = gpu_run(8, 4, 3000, 18, beta=0.4, max_chunk=333)
+    check_estimate(est, sg, ln, fl)
+
+
+def test_sweep_cap_reports_enoconv():
+    # the Jacobi route with one sweep allowed: the cap is hit, mctrg_run
+    # returns ENOCONV with the estimate still written, and the trajectories
+    # whose SVDs hit it carry the NOCONV flag
+    T0 = generic_tensor(2, seed=21)
+    ctx = mctrg.mctrg_create(mctrg.make_options(svd=mctrg.SVD_JACOBI, max_sweeps=1))
+    try:
+        assert mctrg.mctrg_init_tensor(ctx, T0, 2, 8, 4) == 0
+        n = 64
+        ln, sg, fl = np.zeros(n), np.zeros(n, np.int8), np.zeros(n, np.uint8)
+        st, est = mctrg.mctrg_run(ctx, n, 77, 0, ln, sg, fl)
+        assert st == mctrg.MCTRG_ENOCONV and est.status == mctrg.MCTRG_ENOCONV
+        assert np.any(fl & mctrg.FLAG_NOCONV)
+        assert est.n == n and np.all(np.isfinite(ln[sg != 0]))
     finally:
         mctrg.mctrg_destroy(ctx)
