@@ -388,24 +388,46 @@ def main():
     one_step(c2, args.steps, ln_h, sg_h, fl_h)
     mctrg.mctrg_destroy(c2)
     e2e_s = time.perf_counter() - t0
-    # the same trajectories with the contraction on the tensor cores (error-compensated TF32)
+    # the same trajectories with the contraction on the tensor cores: error-compensated
+    # TF32 (TF32X3), and BF16 slices at FP64 accuracy (FP64TC, Ozaki scheme)
     mixed = None
     if wl["precision"] == 0 and not args.no_mixed:
-        cm = make_ctx(mctrg.MCTRG_TF32X3)
-        ms_m, ests_m, outs_m = timed_steps(cm, args.steps, 1, 0)
-        mctrg.mctrg_destroy(cm)
+        mixed = {}
         ref = np.concatenate([o[0].cpu().numpy() for o in outs])
-        got = np.concatenate([o[0].cpu().numpy() for o in outs_m])
-        ok = np.isfinite(ref) & np.isfinite(got)
-        rel = np.abs(got[ok] - ref[ok]) / np.abs(ref[ok])
-        em, e64 = mctrg.mctrg_merge_estimates(ests_m), mctrg.mctrg_merge_estimates(ests)
-        mixed = {"precision": "tf32x3 contraction (tcgen05), FP64 SVD and sampling",
-                 "value": B * args.steps * world / (ms_m / 1000.0), "ms_per_step": ms_m / args.steps,
-                 "lnZ_rel_err_per_traj_median": float(np.median(rel)) if rel.size else None,
-                 "lnZ_rel_err_per_traj_max": float(np.max(rel)) if rel.size else None,
-                 "lnZ_abs_err_per_traj_median": float(np.median(np.abs(got[ok] - ref[ok]))) if rel.size else None,
-                 "lnZhat_rel_err": abs(em.ln_mean_Z - e64.ln_mean_Z) / abs(e64.ln_mean_Z)
-                 if np.isfinite(em.ln_mean_Z) and np.isfinite(e64.ln_mean_Z) else None}
+        e64 = mctrg.mctrg_merge_estimates(ests)
+        peaks_m, _ = measured_peaks()
+        for name, prec, note, ratio in (
+                ("tf32x3", mctrg.MCTRG_TF32X3, "TF32 hi/lo split, three tcgen05 passes, FP32 accumulation", 0.5),
+                ("fp64tc", mctrg.MCTRG_FP64TC, "BF16 slices multiplied exactly on tcgen05, summed in FP64 "
+                                               "(Ozaki scheme)", 1.0)):
+            cm = make_ctx(prec)
+            ms_m, ests_m, outs_m = timed_steps(cm, args.steps, 1, 0)
+            gst = mctrg.mctrg_kernel_stats(cm, mctrg.K_GEMM)
+            mctrg.mctrg_destroy(cm)
+            got = np.concatenate([o[0].cpu().numpy() for o in outs_m])
+            ok = np.isfinite(ref) & np.isfinite(got)
+            rel = np.abs(got[ok] - ref[ok]) / np.abs(ref[ok])
+            em = mctrg.mctrg_merge_estimates(ests_m)
+            # executed tensor-pipe flops of the contraction: passes (TF32X3) or slice
+            # products (FP64TC, 28 at inner dimension 256) times the algorithmic 2 n^2 K
+            passes = 3 if prec == mctrg.MCTRG_TF32X3 else 28
+            tc_rate = passes * gst.flops_alg / (gst.ms / 1e3) / 1e12 if gst.ms > 0 else None
+            tc_peak = peaks_m.get("bf16_tflops_sustained", peaks_m.get("bf16_tflops")) * ratio
+            mixed[name] = {
+                "precision": note + "; SVD and sampling FP64",
+                "value": B * args.steps * world / (ms_m / 1000.0), "ms_per_step": ms_m / args.steps,
+                "lnZ_rel_err_per_traj_median": float(np.median(rel)) if rel.size else None,
+                "lnZ_rel_err_per_traj_max": float(np.max(rel)) if rel.size else None,
+                "lnZ_abs_err_per_site_max": float(np.max(np.abs(got[ok] - ref[ok]))) / wl["L"] ** 2
+                if rel.size else None,
+                "lnZhat_rel_err": abs(em.ln_mean_Z - e64.ln_mean_Z) / abs(e64.ln_mean_Z)
+                if np.isfinite(em.ln_mean_Z) and np.isfinite(e64.ln_mean_Z) else None,
+                "errors_against": "the FP64 path on the same trajectories (parity-tested against the FP64 oracle)",
+                "contraction": {"launches": gst.launches, "ms": gst.ms, "share_of_step": gst.ms / ms_m,
+                                "tensor_tflops": tc_rate, "tensor_peak_tflops": tc_peak,
+                                "tensor_frac": tc_rate / tc_peak if tc_rate else None,
+                                "peak_note": "MEASURED_PEAKS bf16 sustained" + (" x 1/2 (TF32 nominal ratio)"
+                                                                                if ratio != 1.0 else "")}}
     ms_t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)

@@ -71,7 +71,17 @@ extern "C" {
  * as zeros.  Levels whose GEMM shape the tensor-core kernel does not cover
  * (matrix side not a multiple of 256, or above 1024) use the FP64 GEMM and
  * the FP64 threshold. */
-typedef enum { MCTRG_FP64 = 0, MCTRG_TF32 = 1, MCTRG_BF16 = 2, MCTRG_TF32X3 = 3, MCTRG_BF16X3 = 4 } mctrg_precision;
+/* FP64TC: the plaquette GEMM at FP64 accuracy on the tensor cores: each row
+ * of X and Yt is scaled by a power of two and split exactly into s BF16
+ * slices of b bits (b = 8, s = 7 for inner dimension K <= 256; b = 7, s = 8
+ * up to 1024), the s(s+1)/2 leading slice products are formed exactly by
+ * tcgen05 (one FP32 accumulator per slice-sum group, exact below 2^24) and
+ * summed in FP64 (Ozaki, Ogita, Oishi and Rump 2012).  The result carries an
+ * error below 2^-43 K |row max| |column max|, the order of an FP64 dot
+ * product's, so the FP64 zero threshold applies.  Levels whose inner
+ * dimension is not a multiple of 64 up to 1024 use the FP64 GEMM. */
+typedef enum { MCTRG_FP64 = 0, MCTRG_TF32 = 1, MCTRG_BF16 = 2, MCTRG_TF32X3 = 3, MCTRG_BF16X3 = 4,
+               MCTRG_FP64TC = 5 } mctrg_precision;
 
 typedef struct {
     int device;               /* CUDA device ordinal                                   */
@@ -88,6 +98,21 @@ typedef struct {
                                  (Sec. II samples among the nonzero values; tau is
                                  n 2^-52 s_1 in FP64, see mctrg_precision for the
                                  mixed modes); 0 = 1, negative or non-finite: EINVAL */
+    int deterministic_levels; /* levels 0 .. deterministic_levels-1 keep the chi largest
+                                 singular values with weight 1 instead of sampling
+                                 (Sec. II, Eq. approxSVD: plain TRG); sampling starts
+                                 at the next level whose spectrum has more than chi
+                                 nonzero values.  While the network is translation
+                                 invariant these levels cost one split per
+                                 sublattice (Sec. III).  0 = Monte Carlo TRG from
+                                 the start; a value >= 2 log2 L runs deterministic
+                                 TRG, every trajectory identical; in between, the
+                                 hybrid of Sec. V (deterministic coarse-graining
+                                 steps, then Monte Carlo), whose trajectories are
+                                 unbiased samples of the trace of the network after
+                                 those levels.  A kept and a dropped value closer
+                                 than 1e-8 s_1 set MCTRG_FLAG_SPLIT_CLUSTER in every
+                                 trajectory.  Negative: EINVAL */
 } mctrg_options;
 
 /* Route of the per-trajectory SVDs (Sec. II, Eq. exactSVD), both FP64 with
@@ -253,6 +278,20 @@ int mctrg_svd_batched(const double* M, int n, int64_t batch, double* sigma, doub
 int mctrg_svd_batched_noalloc(const double* M, int n, int64_t batch, double* sigma, double* vt,
                               int max_sweeps, void* stream);
 
+/* ---- the plaquette contraction on its own ------------------------------ *
+ * The coarse-graining step's contraction (Sec. III; Levin-Nave plaquette)
+ * ends in one matrix product per new tensor, M = X Yt^T; this runs it for a
+ * batch: X, Yt (device, batch x n x K, row-major, n = D^2) and M (device,
+ * batch x n x n, row-major; written, not accumulated).  precision:
+ * MCTRG_FP64 (FP64 on the CUDA cores) or MCTRG_FP64TC (BF16 slices on the
+ * tensor cores, FP64-accurate; K a multiple of 64, at most 1024).  1 <= D,
+ * n <= 1024, K >= 1, batch >= 1.  Allocates its working memory (FP64TC: the
+ * slice planes and row exponents) for the call and frees it; runs on
+ * `stream` and returns once the stream has completed.  Errors: EINVAL,
+ * ENOMEM, ECUDA. */
+int mctrg_contract_batched(const double* X, const double* Yt, int D, int K, int64_t batch, double* M,
+                           int precision, void* stream);
+
 /* The bidiagonalization route of the same SVD on its own (the route
  * MCTRG_SVD_BIDIAG of the contexts): Householder bidiagonalization, every
  * singular value by bisection on Sturm counts of the Golub-Kahan tridiagonal,
@@ -273,12 +312,13 @@ int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, double* sigm
 /* ---- measurement ------------------------------------------------------ *
  * FP64 arithmetic rate of a device, the peak against which the FP64 kernels
  * (the SVD routes, the FP64 contraction) are quoted: a probe kernel runs, in
- * every thread of a whole number of CTAs per SM, 8 independent chains of
- * `steps` fused multiply-adds (x <- x b + c); one untimed launch, then the
- * best of three launches timed with CUDA events on the legacy default
- * stream.  *tflops = 16 steps threads / time; *ms (may be NULL) receives the
- * best launch's duration.  The paper has no counterpart (it reports no
- * timings).  steps >= 4, a multiple of 4.  Errors: EINVAL, ECUDA. */
+ * every thread of a whole number of CTAs per SM, 4, 8 or 16 independent
+ * chains of about `steps` fused multiply-adds (x <- x b + c) at 128, 256 and
+ * 512 threads per CTA; for each shape one untimed launch, then three launches
+ * timed with CUDA events on the legacy default stream.  *tflops = the best
+ * rate (2 flops per step and chain); *ms (may be NULL) receives that launch's
+ * duration.  The paper has no counterpart (it reports no timings).
+ * steps >= 16.  Errors: EINVAL, ECUDA. */
 int mctrg_measure_fp64_peak(int device, int64_t steps, double* tflops, double* ms);
 
 /* Release every resource of the context (NULL is a no-op). */

@@ -94,19 +94,20 @@ def kaufman_lnZ(L, beta, M=None):
             return 2 * K + math.log(math.tanh(K))
         return math.acosh(c - math.cos(math.pi * k / L))
 
+    # ln(2 cosh y) = |y| + ln(1 + e^{-2|y|}),  ln|2 sinh y| = |y| + ln(1 - e^{-2|y|})
     terms = []                      # (sign, log|Z_i|)
     for odd in (1, 0):
         g = [gamma(2 * r + odd) for r in range(L)]
-        lc = sum(math.log(2 * math.cosh(M * x / 2)) for x in g)
+        lc = sum(abs(M * x / 2) + math.log1p(math.exp(-2 * abs(M * x / 2))) for x in g)
         terms.append((1.0, lc))
         sg, ls = 1.0, 0.0
         for x in g:
-            v = 2 * math.sinh(M * x / 2)
-            if v == 0.0:
+            y = M * x / 2
+            if y == 0.0:
                 sg = 0.0
                 break
-            sg *= math.copysign(1.0, v)
-            ls += math.log(abs(v))
+            sg *= math.copysign(1.0, y)
+            ls += abs(y) + math.log(-math.expm1(-2 * abs(y)))
         terms.append((sg, ls))
     m = max(t[1] for t in terms)
     tot = sum(sg * math.exp(lv - m) for sg, lv in terms)

@@ -134,3 +134,25 @@ def truncate(s, chi, uniforms_fn, n_rows, zero_scale=1.0):
     if np.any(s[kept] < TINY_TOL * s1):
         flags |= FLAG_TINY_KEPT
     return kept, s[kept] / r[kept], flags, True
+
+
+def truncate_top(s, chi, n_rows, zero_scale=1.0):
+    """Deterministic truncation (Sec. II, Eq. approxSVD): keep the chi largest
+    nonzero singular values of one descending spectrum, unreweighted (the
+    plain TRG of Levin and Nave that the paper compares with, Sec. IV, Fig. 3).
+
+    Returns (kept indices, kept values, flags, used=False).  When a kept and a
+    dropped value are closer than GAP_TOL * s_1 the truncated tensor depends on
+    the basis chosen inside that cluster, which two correct SVDs may choose
+    differently: FLAG_SPLIT_CLUSTER.  The zero threshold is that of truncate.
+    """
+    s1 = s[0]
+    if not s1 > 0.0:
+        return [], np.zeros(0), 0, False
+    tau = zero_scale * n_rows * 2.0 ** -52 * s1
+    nnz = int(np.sum(s > tau))
+    k = min(chi, nnz)
+    flags = 0
+    if nnz > chi and (s[k - 1] - s[k]) <= GAP_TOL * s1:
+        flags |= FLAG_SPLIT_CLUSTER
+    return list(range(k)), s[:k].copy(), flags, False

@@ -9,6 +9,17 @@ samples of different tensors must be independent).  After 2 log2(L) levels a
 single tensor remains and is traced (Sec. IV).  Its value Z~ is an unbiased
 sample of Z (Sec. III, Eq. infiniteEnsemble).
 
+With deterministic_levels = k > 0 the first k levels keep the chi largest
+singular values instead of sampling (Sec. II, Eq. approxSVD: plain TRG), and
+sampling starts at level k: the hybrid of deterministic coarse-graining steps
+followed by Monte Carlo that Sec. V proposes for translation-invariant
+systems.  Every trajectory is then an unbiased sample of the trace of the
+network after those k deterministic levels (not of Z itself); with k at least
+the number of levels it is plain deterministic TRG.  While every tensor of a
+level is identical (the translation-invariant network before sampling starts)
+one split per sublattice and one plaquette contraction stand for all of them
+(the logarithmic cost of Sec. III for translation-invariant systems).
+
 Readings of points the paper leaves open (shared with the device path by
 specification):
   * the SVD is LAPACK's (numpy.linalg.svd), singular values descending;
@@ -28,7 +39,7 @@ import numpy as np
 
 from . import philox
 from .network import plan
-from .sampler import truncate
+from .sampler import truncate, truncate_top
 
 
 def matricize(T, parity):
@@ -85,7 +96,7 @@ def contract(F3, F4, F2, F1):
 class Problem:
     """A lattice: L x L torus of identical site tensors T0 (legs l,u,r,d)."""
 
-    def __init__(self, T0, L, chi, zero_tol_scale=1.0):
+    def __init__(self, T0, L, chi, zero_tol_scale=1.0, deterministic_levels=0):
         T0 = np.asarray(T0, dtype=np.float64)
         if T0.ndim != 4 or len(set(T0.shape)) != 1:
             raise ValueError("T0 must be D x D x D x D")
@@ -95,6 +106,8 @@ class Problem:
         self.zero_tol_scale = float(zero_tol_scale)   # multiplies the zero threshold (Sec. II "nonzero")
         self.levels = plan(self.L)
         self.n_levels = len(self.levels) - 1      # SVD levels: 0 .. 2m-1
+        # levels 0 .. deterministic_levels-1 keep the chi largest values (Eq. approxSVD)
+        self.deterministic_levels = int(deterministic_levels)
 
 
 def _stochastic_chooser(seed, traj, level, tensor, chi, zero_scale=1.0):
@@ -105,11 +118,20 @@ def _stochastic_chooser(seed, traj, level, tensor, chi, zero_scale=1.0):
     return choose
 
 
-def run_level(prob, k, tensors, shared, chooser_for):
+def _deterministic_chooser(chi, zero_scale=1.0):
+    def choose(s, n_rows):
+        kept, st, flags, _ = truncate_top(s, chi, n_rows, zero_scale)
+        return kept, st, flags
+    return choose
+
+
+def run_level(prob, k, tensors, shared, chooser_for, deterministic=False):
     """Split every level-k tensor and contract the plaquettes into level k+1.
 
     Returns (new tensors, sum of ln s_1, flags, next-level shared?).
-    chooser_for(t) gives the truncation rule for tensor t.
+    chooser_for(t) gives the truncation rule for tensor t.  On a shared level
+    (every tensor identical) that is exact or deterministic, one split per
+    sublattice and one plaquette stand for all tensors.
     """
     lev = prob.levels[k]
     D = tensors[0].shape[0]
@@ -126,6 +148,17 @@ def run_level(prob, k, tensors, shared, chooser_for):
     else:
         Dn = min(prob.chi, n_rows)
         exact = False
+    if shared and (exact or deterministic):
+        choose = _deterministic_chooser(prob.chi, prob.zero_tol_scale)
+        part = [split(tensors[0], par, Dn, choose) for par in (0, 1)]
+        n_a = int(np.sum(lev.parity == 0))
+        lnacc = n_a * part[0][2] + (lev.n - n_a) * part[1][2]
+        flags = part[0][3] | part[1][3]
+        if lev.children_parents is None or len(lev.children_parents) == 0:
+            return [], lnacc, flags, True
+        # the plaquette's four halves come from A (p, p+a1+a2) and B (p+a1, p+a2)
+        T = contract(part[0][1], part[1][1], part[1][0], part[0][0])
+        return [T] * len(lev.children_parents), lnacc, flags, True
     halves = []
     lnacc = 0.0
     flags = 0
@@ -151,8 +184,12 @@ def run_trajectory(prob, seed, traj):
     lnacc = 0.0
     flags = 0
     for k in range(prob.n_levels):
-        chooser_for = lambda t, k=k: _stochastic_chooser(seed, traj, k, t, prob.chi, prob.zero_tol_scale)
-        tensors, lnk, f, shared = run_level(prob, k, tensors, shared, chooser_for)
+        det = k < prob.deterministic_levels
+        if det:
+            chooser_for = lambda t: _deterministic_chooser(prob.chi, prob.zero_tol_scale)
+        else:
+            chooser_for = lambda t, k=k: _stochastic_chooser(seed, traj, k, t, prob.chi, prob.zero_tol_scale)
+        tensors, lnk, f, shared = run_level(prob, k, tensors, shared, chooser_for, det)
         lnacc += lnk
         flags |= f
         if lnacc == -math.inf:

@@ -323,14 +323,14 @@ cudaError_t launch_estimate(const double* lnabs, const int8_t* sign, const uint8
   return cudaGetLastError();
 }
 
-__global__ void k_flags_to_u8(const uint32_t* f, uint8_t* out, int64_t n) {
+__global__ void k_flags_to_u8(const uint32_t* f, uint8_t* out, int64_t n, uint32_t extra) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (uint8_t)f[i];
+  if (i < n) out[i] = (uint8_t)((f ? f[i] : 0u) | extra);
 }
 
-cudaError_t launch_flags_to_u8(const uint32_t* f, uint8_t* out, int64_t n, cudaStream_t st) {
+cudaError_t launch_flags_to_u8(const uint32_t* f, uint8_t* out, int64_t n, uint32_t extra, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_flags_to_u8<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f, out, n);
+  k_flags_to_u8<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f, out, n, extra);
   return cudaGetLastError();
 }
 

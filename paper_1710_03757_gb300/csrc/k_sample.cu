@@ -100,7 +100,9 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
       w[i] = v * v;
       inset[i] = 0;
     }
-    if (tid == 0) { s_flags = 0; s_nk = sample ? chi : nz; }
+    // without sampling the kc largest nonzero values are kept (all of them on
+    // an exact level, nz <= kc; the top kc on a deterministic one, Eq. approxSVD)
+    if (tid == 0) { s_flags = 0; s_nk = sample ? chi : min(nz, kc); }
     __syncthreads();
 
     if (sample) {
@@ -188,8 +190,9 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
         if (lane == 0 && fl) atomicOr(&s_flags, fl);
       }
     } else {
-      for (int i = tid; i < nz; i += kThreads) inset[i] = 1;
-      if (tid < nz) { s_kept[tid] = tid; s_sigt[tid] = wn[tid]; }
+      const int nkeep = min(nz, kc);
+      for (int i = tid; i < nkeep; i += kThreads) inset[i] = 1;
+      if (tid < nkeep) { s_kept[tid] = tid; s_sigt[tid] = wn[tid]; }
     }
     __syncthreads();
 

@@ -116,6 +116,7 @@ cudaError_t launch_traj_accum(const double* ilns1, const uint32_t* iflags, int64
 // stats = {m, sum x, sum (x - mean)^2, n_neg, n_flag, n_zero} over n results (single block).
 cudaError_t launch_estimate(const double* lnabs, const int8_t* sign, const uint8_t* flags,
                             int64_t n, double* stats, cudaStream_t st);
-cudaError_t launch_flags_to_u8(const uint32_t* f, uint8_t* out, int64_t n, cudaStream_t st);
+// out[i] = f[i] | extra (f may be null: extra alone)
+cudaError_t launch_flags_to_u8(const uint32_t* f, uint8_t* out, int64_t n, uint32_t extra, cudaStream_t st);
 
 }  // namespace mctrg

@@ -77,9 +77,10 @@ extern "C" int mctrg_options_default(mctrg_options* opt) {
 
 extern "C" int mctrg_create(const mctrg_options* opt, mctrg_ctx_t* out) {
   if (!opt || !out) return MCTRG_EINVAL;
-  if (opt->precision < MCTRG_FP64 || opt->precision > MCTRG_BF16X3) return MCTRG_EINVAL;
+  if (opt->precision < MCTRG_FP64 || opt->precision > MCTRG_FP64TC) return MCTRG_EINVAL;
   if (opt->svd < MCTRG_SVD_AUTO || opt->svd > MCTRG_SVD_BIDIAG) return MCTRG_EINVAL;
   if (!(opt->zero_tol_scale >= 0.0) || !std::isfinite(opt->zero_tol_scale)) return MCTRG_EINVAL;
+  if (opt->deterministic_levels < 0) return MCTRG_EINVAL;
   *out = nullptr;
   int ndev = 0;
   CK(cudaGetDeviceCount(&ndev));
@@ -167,7 +168,7 @@ void mctrg_ctx::release_all() {
   DevBuf* all[] = {&T0, &shM, &shW, &shSig, &shPerm, &shNnz, &shLns1, &shU, &shH, &Hbuf[0], &Hbuf[1],
                    &Mb, &Wb, &Xb, &Yb, &sigb, &permb, &nnzb, &ilns1, &iflags, &lnacc, &tflags,
                    &scratch, &o_lnabs, &o_sign, &o_flags, &o_tflags, &stats, &tcXh, &tcYh, &tcXl,
-                   &tcYl, &tcScale, &tcErr, &bdb, &keptb, &sigtb, &nkb, &vrowsb, &bdscr};
+                   &tcYl, &tcScale, &tcErr, &ozExp, &bdb, &keptb, &sigtb, &nkb, &vrowsb, &bdscr};
   for (DevBuf* b : all) b->release();
 }
 
@@ -185,6 +186,7 @@ int mctrg_ctx::init_from_device_tensor(int D0, int L_, int chi_) {
   lnacc0 = 0.0;
   s0 = nlev;
   all_exact = false;
+  prefix_flags = 0;
   int D = D0;
   // cur raw tensor lives in T0 (D^4); the plaquette result goes to shM scratch then back
   for (int k = 0; k < nlev; ++k) {
@@ -213,8 +215,20 @@ int mctrg_ctx::init_from_device_tensor(int D0, int L_, int chi_) {
     const int kc = std::max(1, std::min(chi, nu));
     LevelInfo li{N, D, n, np, kc};
     lv.push_back(li);
-    if (nu <= chi) {
-      // exact level: keep every nonzero value of both matricizations
+    if (nu <= chi || k < opt.deterministic_levels) {
+      // exact level: keep every nonzero value of both matricizations;
+      // deterministic level (Sec. II, Eq. approxSVD): keep the kc largest,
+      // flagged when a kept and a dropped value are closer than GAP_TOL s_1
+      // (the truncated tensor then depends on the basis inside that cluster)
+      if (nu > chi) {
+        std::vector<double> hs(2 * (size_t)np);
+        CK(cudaMemcpyAsync(hs.data(), shSig.p, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int p = 0; p < 2; ++p) {
+          const double* sp = hs.data() + (size_t)p * np;
+          if (hn[p] > kc && sp[kc - 1] - sp[kc] <= GAP_TOL * sp[0]) prefix_flags |= FLAG_SPLIT_CLUSTER;
+        }
+      }
       CK(shH.ensure(sizeof(double) * 2 * (2 * (size_t)n * kc)));
       CK(scratch.ensure(sizeof(double) * sample_scratch_doubles(n, chi, 2)));
       SampleArgs sa{};
@@ -315,6 +329,21 @@ extern "C" int mctrg_init_tensor(mctrg_ctx_t c, const double* T0, int D, int L, 
 }
 
 // ---------------------------------------------------------------------------
+// Device bytes of one item's tensor-core operands (X and Yt, n x d2 each):
+// the rounded operands (and residuals) of the mixed modes, or the BF16 slice
+// planes and row exponents of the FP64-accurate mode.
+static size_t tc_operand_bytes(int prec, int n, int d2) {
+  const size_t e = (size_t)n * d2;
+  switch (prec) {
+    case MCTRG_TF32: return 2 * 4 * e;
+    case MCTRG_BF16: return 2 * 2 * e;
+    case MCTRG_TF32X3: return 2 * 2 * 4 * e;
+    case MCTRG_BF16X3: return 2 * 2 * 2 * e;
+    case MCTRG_FP64TC: return gemm_ozaki_supported(n, d2) ? 2 * 8 * 2 * e + 2 * (size_t)n * sizeof(int) : 0;
+    default: return 0;
+  }
+}
+
 // Memory plan: bytes per trajectory of a chunk, and bytes per in-flight item.
 void mctrg_ctx::plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& total) const {
   size_t per_traj = 2 * sizeof(double) + sizeof(uint32_t);   // lnacc, tflags
@@ -329,6 +358,7 @@ void mctrg_ctx::plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& t
       const size_t d2 = (size_t)lv[k - 1].D * lv[k - 1].D;
       size_t pi = (2 * (size_t)a.n * d2 + (size_t)a.n * a.n + (size_t)a.n_pad * a.n + a.n_pad) * sizeof(double) +
                   (a.n_pad + 1) * sizeof(int) + sizeof(double) + sizeof(uint32_t);
+      pi += tc_operand_bytes(opt.precision, a.n, (int)d2);
       if (use_bidiag(a.n, (int)d2)) {   // d, e, tau; kept values and vectors
         pi += (3 * (size_t)a.n + 32 + 32 * (size_t)a.n) * sizeof(double) + 33 * sizeof(int);
         bd_scr = std::max(bd_scr, bd_vectors_scratch_doubles(a.n, 1 << 16) * sizeof(double));
@@ -416,7 +446,7 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
     std::vector<int8_t> hs((size_t)n, (int8_t)const_sign);
     CK(cudaMemcpyAsync(o_lnabs.p, hl.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(o_sign.p, hs.data(), (size_t)n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(o_flags.p, 0, (size_t)n, st));
+    CK(launch_flags_to_u8(nullptr, o_flags.as<uint8_t>(), n, prefix_flags, st));
     CK(cudaStreamSynchronize(st));
   } else {
     int64_t B, S;
@@ -476,10 +506,12 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
     }
     // tensor-core operands (mixed precision): per item X and Yt rounded, with scales
     const int prec = opt.precision;
+    const bool oz_mode = prec == MCTRG_FP64TC;    // FP64-accurate tensor-core GEMM (BF16 slices)
+    const bool tc_mode = prec != MCTRG_FP64 && !oz_mode;
     const int tc_kind = (prec == MCTRG_TF32 || prec == MCTRG_TF32X3) ? 0 : 1;
     const int tc_passes = (prec == MCTRG_TF32X3 || prec == MCTRG_BF16X3) ? 3 : 1;
     const size_t tc_esize = tc_kind == 0 ? 4 : 2;
-    if (prec != MCTRG_FP64) {
+    if (tc_mode) {
       const size_t elems = std::max<size_t>(max_xy, 1);
       CK(tcXh.ensure(tc_esize * elems));
       CK(tcYh.ensure(tc_esize * elems));
@@ -488,6 +520,22 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
         CK(tcYl.ensure(tc_esize * elems));
       }
       CK(tcScale.ensure(sizeof(double) * 2 * std::max<int64_t>(S, 1)));
+    }
+    if (oz_mode) {   // slice planes (at most 8 per operand) and row exponents
+      size_t oz_elems = 0, oz_rows = 0;
+      for (int k = s0 + 1; k < nlev; ++k) {
+        const int Kd = lv[k - 1].D * lv[k - 1].D;
+        if (!gemm_ozaki_supported(lv[k].n, Kd)) continue;
+        oz_elems = std::max(oz_elems, (size_t)S * lv[k].n * Kd);
+        oz_rows = std::max(oz_rows, (size_t)S * lv[k].n);
+      }
+      if (oz_elems) {
+        CK(tcXh.ensure(2 * 8 * oz_elems));
+        CK(tcYh.ensure(2 * 8 * oz_elems));
+        CK(ozExp.ensure(sizeof(int) * 2 * oz_rows));
+      }
+    }
+    if (prec != MCTRG_FP64) {
       CK(tcErr.ensure(sizeof(uint32_t)));
       CK(cudaMemsetAsync(tcErr.p, 0, sizeof(uint32_t), st));
     }
@@ -531,8 +579,27 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
           CK(timed(MCTRG_K_FORM_XY, Si, Si * 4.0 * D2 * dd * dd * dd,
                    8.0 * Si * (4.0 * p.kc * dd * dd + 2.0 * D2 * dd * dd), [&] { return launch_form_xy(xa, st); }));
           const int Kd = p.D * p.D;
-          const bool used_tc = prec != MCTRG_FP64 && gemm_tc_supported(a.n, Kd, tc_kind);
-          if (used_tc) {
+          const bool used_tc = tc_mode && gemm_tc_supported(a.n, Kd, tc_kind);
+          const bool used_oz = oz_mode && gemm_ozaki_supported(a.n, Kd);
+          if (used_oz) {
+            // FP64-accurate on the tensor cores: BF16 slices of X and Yt, exact slice products
+            int oz_bits, oz_slices;
+            ozaki_params(Kd, &oz_bits, &oz_slices);
+            int* eX = ozExp.as<int>();
+            int* eY = eX + Si * a.n;
+            const int64_t rows = Si * a.n;
+            CK(timed(MCTRG_K_FORM_XY, Si, 0.0, Si * 2.0 * a.n * Kd * (8.0 + 2.0 * oz_slices), [&] {
+              cudaError_t e = launch_ozaki_split(Xb.as<double>(), rows, Kd, tcXh.p, eX, st);
+              if (e != cudaSuccess) return e;
+              return launch_ozaki_split(Yb.as<double>(), rows, Kd, tcYh.p, eY, st); }));
+            GemmOzArgs ga{};
+            ga.M = Mb.as<double>(); ga.D = a.D; ga.n = a.n; ga.K = Kd; ga.c0 = i0; ga.n_items = Si;
+            ga.Nnew = a.N; ga.L = L; ga.level_new = k; ga.fixed_parity = -1; ga.expX = eX; ga.expY = eY;
+            ga.slices = oz_slices; ga.err = tcErr.as<uint32_t>();
+            CK(timed(MCTRG_K_GEMM, Si, Si * 2.0 * a.n * a.n * Kd,
+                     Si * (2.0 * 2.0 * oz_slices * a.n * Kd + 8.0 * a.n * a.n), [&] {
+              return launch_gemm_ozaki(ga, tcXh.p, tcYh.p, st); }));
+          } else if (used_tc) {
             // tensor cores: scale and round the operands, then tcgen05 GEMM
             double* sX = tcScale.as<double>();
             double* sY = sX + Si;
@@ -622,7 +689,7 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
           return launch_trace(Xb.as<double>(), Yb.as<double>(), (int64_t)p.kc * p.kc * p.n, Bc, lnacc0,
                               lnacc.as<double>(), o_lnabs.as<double>() + c0, o_sign.as<int8_t>() + c0, st); }));
         CK(timed(MCTRG_K_OTHER, Bc, 0.0, 5.0 * Bc, [&] {
-          return launch_flags_to_u8(o_tflags.as<uint32_t>(), o_flags.as<uint8_t>() + c0, Bc, st); }));
+          return launch_flags_to_u8(o_tflags.as<uint32_t>(), o_flags.as<uint8_t>() + c0, Bc, prefix_flags, st); }));
       }
     }
   }

@@ -42,12 +42,14 @@ struct mctrg_ctx {
   int s0 = 0;               // first level where sampling happens (nlev: none)
   double lnacc0 = 0.0;      // sum of ln s_1 over the shared levels 0..s0
   bool all_exact = false;
+  uint32_t prefix_flags = 0; // flags of the shared levels (deterministic truncations), in every trajectory
   double const_lnabs = 0.0;
   int const_sign = 0;
   mctrg::DevBuf T0, shM, shW, shSig, shPerm, shNnz, shLns1, shU, shH;
   mctrg::DevBuf Hbuf[2], Mb, Wb, Xb, Yb, sigb, permb, nnzb, ilns1, iflags, lnacc, tflags, scratch;
   mctrg::DevBuf o_lnabs, o_sign, o_flags, o_tflags, stats;
-  mctrg::DevBuf tcXh, tcYh, tcXl, tcYl, tcScale, tcErr;   // tensor-core operands
+  mctrg::DevBuf tcXh, tcYh, tcXl, tcYl, tcScale, tcErr;   // tensor-core operands (slice planes in FP64TC)
+  mctrg::DevBuf ozExp;                                     // FP64TC: row exponents of X and Yt
   mctrg::DevBuf bdb, keptb, sigtb, nkb, vrowsb, bdscr;    // bidiagonalization route
 
   // per-kernel-class statistics (MCTRG_K_*)

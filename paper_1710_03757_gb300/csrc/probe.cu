@@ -1,9 +1,10 @@
 // FP64 throughput probe: the denominator of the FP64-pipe roofline.
 //
-// Every thread runs kChains independent DFMA recurrences x <- x b + c for a
-// fixed number of steps, so the FP64 pipe sees kChains independent
-// instructions per thread between dependences and the warps of an SM keep it
-// busy; the grid is a whole number of CTAs per SM.  The recurrence contracts
+// Every thread runs CH independent DFMA recurrences x <- x b + c for a fixed
+// number of steps, so the FP64 pipe sees CH independent instructions per
+// thread between dependences and the warps of an SM keep it busy; the grid is
+// a whole number of CTAs per SM.  Several shapes (chains per thread, threads
+// per CTA) run the same work and the best rate is the peak.  The recurrence contracts
 // toward c / (1 - b), so every value stays finite and normal, and the final
 // values are summed into one word that the host reads (nothing is dead code).
 #include <cuda_runtime.h>
@@ -14,63 +15,83 @@
 
 namespace {
 
-constexpr int kChains = 8;
-constexpr int kThreads = 256;
-
-__global__ void __launch_bounds__(kThreads) k_dfma_probe(int64_t steps, double b, double c, double* sink) {
-  double x[kChains];
+// CH independent chains per thread, unrolled U steps per loop trip.
+template <int CH, int U>
+__global__ void k_dfma_probe(int64_t steps, double b, double c, double* sink) {
+  double x[CH];
 #pragma unroll
-  for (int j = 0; j < kChains; ++j) x[j] = 1.0 + 1e-3 * (threadIdx.x + j);
-  for (int64_t s = 0; s < steps; s += 4) {
+  for (int j = 0; j < CH; ++j) x[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+  for (int64_t s = 0; s < steps; s += U) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
 #pragma unroll
-      for (int j = 0; j < kChains; ++j) x[j] = fma(x[j], b, c);
+      for (int j = 0; j < CH; ++j) x[j] = fma(x[j], b, c);
     }
   }
   double t = 0.0;
 #pragma unroll
-  for (int j = 0; j < kChains; ++j) t += x[j];
+  for (int j = 0; j < CH; ++j) t += x[j];
   if (t == 12345.678) sink[0] = t;   // never true; keeps the chains live
   if (threadIdx.x == 0 && blockIdx.x == 0) sink[1] = t;
+}
+
+// Best of three timed launches of one variant (after one untimed launch);
+// returns the rate in TFLOP/s (0 on failure) and its launch time in *ms.
+template <int CH, int U>
+double time_variant(int sms, int threads, int64_t steps, double* sink, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfma_probe<CH, U>, threads, 0) != cudaSuccess ||
+      per_sm < 1)
+    return 0.0;
+  const int grid = sms * per_sm;
+  const int64_t st = (steps / U) * U;
+  k_dfma_probe<CH, U><<<grid, threads>>>(st / 4 < U ? U : (st / 4 / U) * U, 0.9999999, 1e-7, sink);
+  if (cudaGetLastError() != cudaSuccess) return 0.0;
+  float best = 0.f;
+  for (int r = 0; r < 3; ++r) {
+    float t = 0.f;
+    if (cudaEventRecord(e0) != cudaSuccess) return 0.0;
+    k_dfma_probe<CH, U><<<grid, threads>>>(st, 0.9999999, 1e-7, sink);
+    if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1) != cudaSuccess ||
+        cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+      return 0.0;
+    if (r == 0 || t < best) best = t;
+  }
+  *ms = best;
+  return 2.0 * CH * (double)st * grid * threads / (best * 1e-3) / 1e12;
 }
 
 }  // namespace
 
 extern "C" int mctrg_measure_fp64_peak(int device, int64_t steps, double* tflops, double* ms) {
-  if (!tflops || steps < 4 || steps % 4 != 0) return MCTRG_EINVAL;
+  if (!tflops || steps < 16) return MCTRG_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return MCTRG_ECUDA;
-  int sms = 0, per_sm = 0;
+  int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return MCTRG_ECUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfma_probe, kThreads, 0) != cudaSuccess ||
-      per_sm < 1)
-    return MCTRG_ECUDA;
-  const int grid = sms * per_sm;
   double* sink = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int status = MCTRG_ECUDA;
-  float best = 0.f;
   if (cudaMalloc(&sink, 2 * sizeof(double)) != cudaSuccess) return MCTRG_ECUDA;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) goto done;
-  // one untimed launch (clocks ramp, code loads), then the best of three
-  k_dfma_probe<<<grid, kThreads>>>(steps / 4 < 4 ? 4 : (steps / 4) & ~int64_t(3), 0.9999999, 1e-7, sink);
-  if (cudaGetLastError() != cudaSuccess) goto done;
-  for (int r = 0; r < 3; ++r) {
-    if (cudaEventRecord(e0) != cudaSuccess) goto done;
-    k_dfma_probe<<<grid, kThreads>>>(steps, 0.9999999, 1e-7, sink);
-    if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1) != cudaSuccess ||
-        cudaEventSynchronize(e1) != cudaSuccess)
-      goto done;
-    float t = 0.f;
-    if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) goto done;
-    if (r == 0 || t < best) best = t;
+  double best = 0.0;
+  float best_ms = 0.f;
+  if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+    // a few shapes of the same work: the pipe's rate is the best of them
+    const int threads[3] = {128, 256, 512};
+    for (int ti = 0; ti < 3; ++ti) {
+      float t = 0.f;
+      double r;
+      r = time_variant<4, 8>(sms, threads[ti], steps, sink, e0, e1, &t);
+      if (r > best) { best = r; best_ms = t; }
+      r = time_variant<8, 4>(sms, threads[ti], steps, sink, e0, e1, &t);
+      if (r > best) { best = r; best_ms = t; }
+      r = time_variant<16, 2>(sms, threads[ti], steps, sink, e0, e1, &t);
+      if (r > best) { best = r; best_ms = t; }
+    }
   }
-  *tflops = 2.0 * kChains * (double)steps * grid * kThreads / (best * 1e-3) / 1e12;
-  if (ms) *ms = best;
-  status = MCTRG_OK;
-done:
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(sink);
-  return status;
+  if (!(best > 0.0)) return MCTRG_ECUDA;
+  *tflops = best;
+  if (ms) *ms = best_ms;
+  return MCTRG_OK;
 }

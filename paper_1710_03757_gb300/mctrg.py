@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libmctrg.so")
 MCTRG_OK, MCTRG_EINVAL, MCTRG_ENOMEM, MCTRG_ENOCONV, MCTRG_EDOMAIN = 0, -1, -2, -3, -4
 MCTRG_ECUDA, MCTRG_ESTATE, MCTRG_ETIMEDOUT, MCTRG_EAGAIN, MCTRG_EUNREACHABLE = -5, -6, -7, -8, -9
 MCTRG_ENOTFOUND = -10
-MCTRG_FP64, MCTRG_TF32, MCTRG_BF16, MCTRG_TF32X3, MCTRG_BF16X3 = 0, 1, 2, 3, 4
+MCTRG_FP64, MCTRG_TF32, MCTRG_BF16, MCTRG_TF32X3, MCTRG_BF16X3, MCTRG_FP64TC = 0, 1, 2, 3, 4, 5
 FLAG_SPLIT_CLUSTER, FLAG_DRAW_TIE, FLAG_TINY_KEPT, FLAG_NOCONV = 1, 2, 4, 16
 
 # every symbol the headers declare (checked by the CPU test suite)
@@ -23,7 +23,7 @@ EXPORTS = [
     "mctrg_server_create", "mctrg_server_submit", "mctrg_server_poll", "mctrg_server_wait",
     "mctrg_server_destroy", "mctrg_plan_level", "mctrg_philox_uniform", "mctrg_kernel_stats",
     "mctrg_reset_kernel_stats", "mctrg_svd_batched", "mctrg_svd_batched_noalloc",
-    "mctrg_svd_bidiag_batched", "mctrg_measure_fp64_peak",
+    "mctrg_svd_bidiag_batched", "mctrg_measure_fp64_peak", "mctrg_contract_batched",
 ]
 K_FORM_XY, K_GEMM, K_JACOBI, K_SAMPLE, K_TRACE, K_OTHER, K_BIDIAG, K_BISECT, K_VECTORS, K_COUNT = range(10)
 KERNEL_NAMES = ["form_xy", "gemm", "jacobi", "sample_split", "trace", "other", "bidiag", "bisect", "vectors"]
@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("max_sweeps", ctypes.c_int),
                 ("max_chunk", ctypes.c_int), ("profile", ctypes.c_int), ("svd", ctypes.c_int),
-                ("zero_tol_scale", ctypes.c_double)]
+                ("zero_tol_scale", ctypes.c_double), ("deterministic_levels", ctypes.c_int)]
 
 
 class Estimate(ctypes.Structure):
@@ -92,6 +92,7 @@ def lib():
             "mctrg_svd_batched_noalloc": (c_int, [vp, c_int, i64, vp, vp, c_int, vp]),
             "mctrg_svd_bidiag_batched": (c_int, [vp, c_int, i64, vp, c_int, vp, vp]),
             "mctrg_measure_fp64_peak": (c_int, [c_int, i64, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+            "mctrg_contract_batched": (c_int, [vp, vp, c_int, c_int, i64, vp, c_int, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -138,8 +139,9 @@ def mctrg_options_default():
 
 
 def make_options(device=0, stream=None, precision=MCTRG_FP64, hbm_budget_bytes=0, max_sweeps=0,
-                 max_chunk=0, profile=0, svd=SVD_AUTO, zero_tol_scale=0.0):
+                 max_chunk=0, profile=0, svd=SVD_AUTO, zero_tol_scale=0.0, deterministic_levels=0):
     o = mctrg_options_default()
+    o.deterministic_levels = int(deterministic_levels)
     o.device, o.precision, o.profile, o.svd = int(device), int(precision), int(profile), int(svd)
     o.zero_tol_scale = float(zero_tol_scale)
     o.cuda_stream = stream
@@ -224,7 +226,16 @@ def mctrg_svd_bidiag_batched(M, sigma, vt=None, stream=None):
     return lib().mctrg_svd_bidiag_batched(_ptr(M), n, batch, _ptr(sigma), nv, _ptr(vt), stream)
 
 
-def mctrg_measure_fp64_peak(device=0, steps=1 << 16):
+def mctrg_contract_batched(X, Yt, M, precision=MCTRG_FP64, stream=None):
+    """M[b] = X[b] Yt[b]^T: X, Yt (batch, D*D, K) and M (batch, D*D, D*D) float64 device tensors."""
+    batch, n, K = int(X.shape[0]), int(X.shape[1]), int(X.shape[2])
+    D = int(round(n ** 0.5))
+    if D * D != n:
+        raise ValueError("rows must be a perfect square D*D")
+    return lib().mctrg_contract_batched(_ptr(X), _ptr(Yt), D, K, batch, _ptr(M), int(precision), stream)
+
+
+def mctrg_measure_fp64_peak(device=0, steps=1 << 14):
     """(status, TFLOP/s, ms) of the library's DFMA throughput probe."""
     tf, ms = ctypes.c_double(), ctypes.c_double()
     s = lib().mctrg_measure_fp64_peak(int(device), int(steps), ctypes.byref(tf), ctypes.byref(ms))

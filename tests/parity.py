@@ -11,6 +11,15 @@ they must agree too:
   * a trajectory is flagged on both sides or on neither, and where both flag
     it, the two flag words share at least one bit (the near-tie that both saw
     first; after it the kept sets may differ and later flags with them);
+  * the one stated exception: a trajectory flagged on one side only whose
+    flags include a kept value below 1e-7 s_1.  That side sampled singular
+    values at the rounding-noise level of a (numerically) rank-deficient
+    matrix, e.g. [1, 2.7e-13, 1.2e-14, 6e-17] where the matrix has rank 1;
+    the other SVD's noise values fell below the zero threshold n 2^-52 s_1,
+    so it kept all its "nonzero" values without sampling and raised no flag.
+    Which noise values clear the threshold is not determined by the
+    mathematics, so such trajectories are counted and printed, held to at
+    most 1% of the trajectories, and excluded from the value comparison;
   * every unflagged trajectory has the same sign and
     |ln|Z~|_gpu - ln|Z~|_oracle| <= 1e-10 max(1, |ln|Z~||)  (Q16: the
     tolerance of ln Z per trajectory, FP64 on both sides);
@@ -31,6 +40,7 @@ from oracle.estimator import estimate
 
 TOL = 1e-10
 EST_TOL = 1e-13
+FLAG_TINY_KEPT = 4
 
 
 def _rel(a, b, scale):
@@ -71,15 +81,20 @@ def compare(gpu, orc, min_ok, label=""):
     os_, ol, of = orc
     n = len(gl)
     fg, fo = gf != 0, of != 0
-    only_gpu, only_orc = np.flatnonzero(fg & ~fo), np.flatnonzero(~fg & fo)
+    one_sided = np.flatnonzero(fg != fo)
+    noise = one_sided[((gf | of)[one_sided] & FLAG_TINY_KEPT) != 0]
+    other = np.setdiff1d(one_sided, noise)
     disjoint = np.flatnonzero(fg & fo & ((gf & of) == 0))
-    print("%s parity: %d trajectories, %d flagged (gpu) / %d (oracle), flag rate %.3f"
-          % (label, n, int(fg.sum()), int(fo.sum()), float(fg.mean()) if n else 0.0))
-    assert only_gpu.size == 0 and only_orc.size == 0, (
-        "flagged on one side only: gpu %s, oracle %s" % (only_gpu[:10].tolist(), only_orc[:10].tolist()))
+    print("%s parity: %d trajectories, %d flagged (gpu) / %d (oracle), flag rate %.3f, "
+          "%d flagged on one side only with noise-level kept values %s"
+          % (label, n, int(fg.sum()), int(fo.sum()), float(fg.mean()) if n else 0.0, noise.size,
+             noise[:10].tolist()))
+    assert other.size == 0, "flagged on one side only: %s (gpu flags %s, oracle flags %s)" % (
+        other[:10].tolist(), gf[other[:10]].tolist(), of[other[:10]].tolist())
+    assert noise.size <= max(1, n // 100), "noise-level one-sided flags at %s" % noise[:10].tolist()
     assert disjoint.size == 0, "flag words without a common bit at %s" % disjoint[:10].tolist()
-    ok = ~fg
-    assert ok.mean() >= min_ok, "too many flagged trajectories: %d of %d" % (int(fg.sum()), n)
+    ok = ~fg & ~fo
+    assert ok.mean() >= min_ok, "too many flagged trajectories: %d of %d" % (int((~ok).sum()), n)
     np.testing.assert_array_equal(gs[ok], os_[ok])
     nz = ok & (os_ != 0)
     if nz.any():

@@ -127,7 +127,7 @@ def test_ising_parity_bidiag(torch, beta, h, L, chi, n):
     seed = 991 + L
     gpu = gpu_run(L, chi, n, seed, beta=beta, h=h, svd=mctrg.SVD_BIDIAG)
     orc = run_many(Problem(ising.site_tensor(beta, h), L, chi), seed, 0, n)
-    compare(gpu, orc, min_ok=0.5, label="bidiag ising b%g h%g L%d chi%d" % (beta, h, L, chi))
+    compare(gpu, orc, min_ok=0.9, label="bidiag ising b%g h%g L%d chi%d" % (beta, h, L, chi))
 
 
 @pytest.mark.parametrize("case", ["ising", "generic3"])
@@ -142,7 +142,8 @@ def test_chi32_parity_n1024_levels(torch, case):
         T0, L, n = generic_tensor(3, seed=9), 8, 6
         gpu = gpu_run(L, 32, n, 31, T0=T0)
     orc = run_many(Problem(T0, L, 32), 31, 0, n, workers=n)
-    compare(gpu, orc, min_ok=0.5, label="chi32 " + case)
+    # measured: Ising none flagged; the D = 3 generic tensor 2 of 6 (kept values below 1e-7 s_1)
+    compare(gpu, orc, min_ok=0.9 if case == "ising" else 0.5, label="chi32 " + case)
 
 
 def test_n64_parity_bidiag(torch):
@@ -158,7 +159,7 @@ def test_ising_chi16_parity_auto_route(torch, L, beta, h, n):
     seed = seed_for(2) + L
     gpu = gpu_run(L, 16, n, seed, beta=beta, h=h)
     orc = run_many(Problem(ising.site_tensor(beta, h), L, 16), seed, 0, n, workers=8)
-    compare(gpu, orc, min_ok=0.5, label="auto ising chi16 L%d" % L)
+    compare(gpu, orc, min_ok=0.9, label="auto ising chi16 L%d" % L)
 
 
 def test_routes_agree_at_L1024(torch):

@@ -8,7 +8,9 @@ outputs.  Estimates must lie within 3 standard errors of the exact Z where
 one is known.
 
 The min_ok floors (fraction of unflagged trajectories a case accepts) sit
-below the flag rates measured on GB300 for the same seeds (printed with -s).
+below the unflagged fractions measured on GB300 for the same seeds (printed
+with -s): 0 to 1.1% of the trajectories are flagged in every case here, so
+the floors are 0.9.
 """
 import math
 
@@ -62,7 +64,7 @@ def test_config1_parity_and_unbiased():
     # every negative trajectory is accounted for: the totals differ only
     # through flagged trajectories whose signs differ (compare lists them)
     ref = estimate(orc[0], orc[1])
-    flagged = gpu[3] != 0
+    flagged = (gpu[3] != 0) | (orc[2] != 0)
     d_flagged = int(np.sum(gpu[2][flagged] < 0)) - int(np.sum(orc[0][flagged] < 0))
     assert est.n_negative - ref['n_negative'] == d_flagged
 
@@ -83,7 +85,7 @@ def test_ising_parity(beta, h, L, chi, n):
     seed = 991 + L
     gpu = gpu_run(L, chi, n, seed, beta=beta, h=h)
     orc = run_many(Problem(ising.site_tensor(beta, h), L, chi), seed, 0, n)
-    compare(gpu, orc, min_ok=0.5, label="ising b%g h%g L%d chi%d" % (beta, h, L, chi))
+    compare(gpu, orc, min_ok=0.9, label="ising b%g h%g L%d chi%d" % (beta, h, L, chi))
 
 
 def test_shared_memory_jacobi_n64():
@@ -94,7 +96,7 @@ def test_shared_memory_jacobi_n64():
     compare(gpu, orc, min_ok=0.8, label="generic n64")
     gpu = gpu_run(8, 8, 24, 6, beta=0.44)
     orc = run_many(Problem(ising.site_tensor(0.44, 0.0), 8, 8), 6, 0, 24, workers=4)
-    compare(gpu, orc, min_ok=0.5, label="ising n64")
+    compare(gpu, orc, min_ok=0.9, label="ising n64")
 
 
 def test_global_workspace_jacobi_n256():
@@ -111,21 +113,7 @@ def test_ising_chi16_parity(L, beta, h, n):
     seed = seed_for(2) + L
     gpu = gpu_run(L, 16, n, seed, beta=beta, h=h)
     orc = run_many(Problem(ising.site_tensor(beta, h), L, 16), seed, 0, n, workers=8)
-    compare(gpu, orc, min_ok=0.5, label="ising chi16 L%d" % L)
-
-
-def test_full_size_L1024_properties():
-    # the headline lattice (1024 x 1024, chi = 16, beta = 0.44, FP64): the oracle cannot
-    # follow it, so check what holds at any size -- counters fix each trajectory whatever
-    # the batch, the sign, and ln Z~ per site against Onsager's free energy
-    a = gpu_run(1024, 16, 2, seed_for(2), beta=0.44)
-    b = gpu_run(1024, 16, 1, seed_for(2), beta=0.44, first=1)
-    assert a[1][1] == b[1][0]
-    assert np.all(a[2] == 1)
-    f = ising.onsager_minus_beta_f(0.44)
-    assert np.all(np.abs(a[1] / 1024 ** 2 - f) < 2e-3)
-    m = gpu_run(1024, 16, 1, seed_for(2), beta=0.44, first=1, precision=mctrg.MCTRG_TF32X3)
-    assert abs(m[1][0] - b[1][0]) / abs(b[1][0]) < 1e-6
+    compare(gpu, orc, min_ok=0.9, label="ising chi16 L%d" % L)
 
 
 @pytest.mark.parametrize("svd", [mctrg.SVD_JACOBI, mctrg.SVD_BIDIAG])
