@@ -140,45 +140,76 @@ def oracle_rate(wl, seconds_budget=20.0, workers=None):
 
 
 def _serve_mix(rng):
-    return (float(rng.uniform(0.3, 0.6)), float(rng.choice([0.0, 0.05])), int(rng.choice([4, 8, 16])),
-            int(rng.choice([2, 4])), float(10 ** rng.uniform(-2, -1)), 1 << 16, int(rng.integers(1 << 62)))
+    """One job of the serving stand-in (small lattices; the literal sizes run as refusals)."""
+    return (float(rng.uniform(0.3, 0.6)), float(rng.choice([0.0, 0.05])), int(rng.choice([4, 8, 16, 32])),
+            int(rng.choice([2, 4, 8])), float(10 ** rng.uniform(-4, -2)), 1 << 18, int(rng.integers(1 << 62)))
 
 
-def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5):
+def _serve_literal(rng):
+    """One job at the serving workload's literal sizes: L in 2^8..2^16, chi in {8, 16, 32},
+    target 1e-6..1e-4 (refused at submission or projected out of reach)."""
+    return (float(rng.uniform(0.3, 0.6)), float(rng.choice([0.0, 0.05])), int(2 ** rng.integers(8, 17)),
+            int(rng.choice([8, 16, 32])), float(10 ** rng.uniform(-6, -4)), 1 << 18, int(rng.integers(1 << 62)))
+
+
+def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_every=20, drain_s=240.0):
     """Continuous batching under Poisson arrivals at a stated fraction of capacity.
 
     Job mix (small-lattice stand-in of the serving workload): beta uniform in
-    [0.3, 0.6], h in {0, 0.05}, L in {4, 8, 16}, chi in {2, 4}, target standard
-    error of ln Z log-uniform in [1e-2, 1e-1], at most 2^16 trajectories.  The
+    [0.3, 0.6], h in {0, 0.05}, L in {4, 8, 16, 32}, chi in {2, 4, 8}, target
+    standard error of ln Z log-uniform in [1e-4, 1e-2], at most 2^18
+    trajectories; every `literal_every`-th arrival is a job at the literal
+    sizes, which must be refused at submission (footprint beyond the device)
+    or stopped after its first round (target projected out of reach).  The
     server's capacity (trajectories/s and trajectories per job) is measured
-    first on a burst of 64 jobs from the same mix; arrivals then come at
-    `load` times the job rate that capacity sustains.
+    first on a burst of 48 jobs from the mix; arrivals then come at `load`
+    times the job rate that capacity sustains.  Jobs still running `drain_s`
+    after the last arrival are reported as unfinished.
     """
     import numpy as np
     rng = np.random.default_rng(seed)
     srv = mctrg.mctrg_server_create()
     try:
         t0 = time.perf_counter()
-        burst = [mctrg.mctrg_server_submit(srv, *_serve_mix(rng))[1] for _ in range(64)]
+        burst = [mctrg.mctrg_server_submit(srv, *_serve_mix(rng))[1] for _ in range(48)]
         traj = sum(mctrg.mctrg_server_wait(srv, j, 900.0)[1].n for j in burst)
         cap = traj / (time.perf_counter() - t0)
-        rate = load * cap / (traj / 64.0)
-        ids, lat, n_traj, reached = [], [], 0, 0
+        rate = load * cap / (traj / 48.0)
+        ids, lit, refused, n_arr = [], [], 0, 0
         t0 = time.perf_counter()
         t_next = 0.0
         while t_next < seconds:
             now = time.perf_counter() - t0
             if now < t_next:
                 time.sleep(t_next - now)
-            st, j = mctrg.mctrg_server_submit(srv, *_serve_mix(rng))
-            if st == 0:
-                ids.append(j)
+            n_arr += 1
+            if literal_every and n_arr % literal_every == 0:
+                ts = time.perf_counter()
+                st, j = mctrg.mctrg_server_submit(srv, *_serve_literal(rng))
+                if st == 0:
+                    lit.append((j, ts))
+                else:
+                    refused += 1
+            else:
+                st, j = mctrg.mctrg_server_submit(srv, *_serve_mix(rng))
+                if st == 0:
+                    ids.append(j)
             t_next += float(rng.exponential(1.0 / rate))
+        t_end = time.perf_counter()
+        lat, n_traj, reached, projected, unfinished = [], 0, 0, 0, 0
         for j in ids:
-            st, est, l = mctrg.mctrg_server_wait(srv, j, 900.0)
+            st, est, l = mctrg.mctrg_server_wait(srv, j, max(1.0, drain_s - (time.perf_counter() - t_end)))
+            if st == mctrg.MCTRG_ETIMEDOUT:
+                unfinished += 1
+                continue
             lat.append(l)
             n_traj += est.n
             reached += st == 0
+            projected += st == mctrg.MCTRG_EUNREACHABLE
+        lit_lat = []
+        for j, ts in lit:
+            st, est, l = mctrg.mctrg_server_wait(srv, j, 600.0)
+            lit_lat.append(l)
         wall = time.perf_counter() - t0
     finally:
         mctrg.mctrg_server_destroy(srv)
@@ -188,8 +219,12 @@ def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5):
             "latency_p50_s": float(lat[len(lat) // 2]) if len(lat) else None,
             "latency_p99_s": float(lat[min(len(lat) - 1, int(0.99 * len(lat)))]) if len(lat) else None,
             "trajectories_per_s": n_traj / wall, "jobs_reaching_target": reached,
-            "mix": "beta U[0.3,0.6], h {0,0.05}, L {4,8,16}, chi {2,4}, target SE(ln Z) 1e-2..1e-1 "
-                   "log-uniform, max 2^16 trajectories"}
+            "jobs_projected_unreachable": projected, "jobs_unfinished_after_drain": unfinished,
+            "literal_jobs": {"refused_at_submit": refused, "projected_out_of_reach": len(lit),
+                             "latency_max_s": max(lit_lat) if lit_lat else None},
+            "mix": "beta U[0.3,0.6], h {0,0.05}, L {4,8,16,32}, chi {2,4,8}, target SE(ln Z) 1e-4..1e-2 "
+                   "log-uniform, max 2^18 trajectories; every %dth arrival at the literal sizes (L 2^8..2^16, "
+                   "chi {8,16,32}, target 1e-6..1e-4)" % literal_every}
 
 
 def measure_uneven(mctrg, n_jobs=32, seed=0xB0A7 + 4):

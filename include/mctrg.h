@@ -328,31 +328,46 @@ void mctrg_destroy(mctrg_ctx_t ctx);
 const char* mctrg_strerror(int status);
 
 /* ---- serving: continuous batching of estimate jobs -------------------- *
- * A server owns one device and a fixed pool of workers, each with its own
- * stream and a persistent context holding an equal share of the device
- * memory budget.  Jobs (beta, h, L, chi, target standard error of ln Z)
- * arrive with mctrg_server_submit at any time; a free worker takes the oldest
- * queued job and advances it in rounds of trajectories (chunked to fit the
- * worker's memory) until its target error or max_samples is reached, so the
- * kernels of all running jobs share the device and a finished job's worker
- * starts the next one at once, reusing its device buffers.  Trajectory i of a
- * job uses counter i under the job's seed, so its result is the same alone
- * and in any mix. */
+ * A server owns one device, a device-memory budget (hbm_budget_bytes of the
+ * options; 0 = 80% of the free memory) and 16 workers (slots), each with its
+ * own stream and a persistent context.  Jobs (beta, h, L, chi, target
+ * standard error of ln Z) arrive with mctrg_server_submit at any time and
+ * are admitted by HBM footprint: a free worker takes the oldest queued job
+ * whose footprint (the memory plan of its largest round of trajectories,
+ * bounded from the largest leg dimensions the lattice can have; see
+ * mctrg_server_footprint) fits the budget that running and idle workers do
+ * not hold; a job passed over 32 times for later, smaller ones blocks the
+ * queue until memory frees.  Workers keep their buffers between jobs and
+ * give them back only when a queued job is blocked on memory.  A job
+ * advances in rounds of trajectories (256 first for L <= 64, 32 for
+ * L <= 256, 4 above; doubling up to 8192); after each round it stops when
+ * its standard error of ln Z reaches the target, or when that error
+ * projected to max_samples by the 1/sqrt(N) law (Sec. V, Eq. shrunkDev)
+ * exceeds twice the target (EUNREACHABLE), or when max_samples is spent.
+ * The kernels of all running jobs share the device on their streams.
+ * Trajectory i of a job uses counter i under the job's seed, so its result
+ * is the same alone and in any mix. */
 typedef struct mctrg_server* mctrg_server_t;
 
 int mctrg_server_create(const mctrg_options* opt, mctrg_server_t* out);
 /* Non-blocking.  target_se_lnZ > 0; max_samples >= 1.  Returns EUNREACHABLE
- * at once when even one trajectory of the job cannot fit a worker's memory. */
+ * at once when even one trajectory of the job cannot fit the server's budget. */
 int mctrg_server_submit(mctrg_server_t srv, double beta, double h, int L, int chi,
                         double target_se_lnZ, int64_t max_samples, uint64_t seed,
                         uint64_t* job_id);
 /* EAGAIN until the job is done; then fills *est and *latency_s (submit to
  * completion, seconds) and forgets the job.  Returns OK when the target error
- * was reached, EUNREACHABLE (est still filled) when max_samples ran out first. */
+ * was reached, EUNREACHABLE (est still filled) when it was projected out of
+ * reach or max_samples ran out first. */
 int mctrg_server_poll(mctrg_server_t srv, uint64_t job_id, mctrg_estimate* est, double* latency_s);
 /* Blocks up to timeout_s; ETIMEDOUT if the job is still running. */
 int mctrg_server_wait(mctrg_server_t srv, uint64_t job_id, double timeout_s,
                       mctrg_estimate* est, double* latency_s);
+/* Device bytes a job (L, chi, max_samples) would be admitted with (*bytes);
+ * EUNREACHABLE when not even one trajectory fits the budget. */
+int mctrg_server_footprint(mctrg_server_t srv, int L, int chi, int64_t max_samples, size_t* bytes);
+/* The server's budget and the bytes its workers hold now (either may be NULL). */
+int mctrg_server_memory(mctrg_server_t srv, size_t* budget, size_t* reserved);
 void mctrg_server_destroy(mctrg_server_t srv);
 
 #ifdef __cplusplus

@@ -3,11 +3,15 @@
 // 2012), with BF16 slices multiplied exactly by tcgen05.mma.
 //
 // Split (k_ozaki_split, one warp per row of X or Yt): with e the exponent of
-// the row's largest magnitude (every |x| < 2^e), t = x 2^{b-1-e} and for
-// i = 0 .. s-1:  a_i = rint(t), t = (t - a_i) 2^b.  Each a_i is an integer
-// with |a_i| <= 2^{b-1} (b <= 8 bits: exact in BF16), t - a_i is exact, and
-// x = 2^e sum_i a_i 2^{-(b-1)-b i} + r with |r| < 2^{e-(b-1)-b(s-1)-1}.  The
-// slice planes hold a_i 2^{-(b-1)-b i} (a power-of-two shift, still exact).
+// the row's largest magnitude (every |x| < 2^e) and P = (b-1) + b(s-1) = 55,
+// the integer F = round(x 2^{P-e}) (|F| <= 2^P, read from the significand and
+// exponent bits with integer shifts) is recoded into signed digits from the
+// bottom, a_i = ((F + 2^{b-1}) mod 2^b) - 2^{b-1}, F <- (F - a_i) / 2^b, the
+// top digit taking the rest, so x = 2^e sum_i a_i 2^{-(b-1)-b i} + r with
+// |r| <= 2^{e-P-1}, |a_i| <= 2^{b-1} (b <= 8 bits: exact in BF16).  Only
+// integer and FP32 operations per element: FP64 issues at 1/64 of the FP32
+// rate on this GPU.  The slice planes hold a_i 2^{-(b-1)-b i} (a power-of-two
+// scaling, still exact).
 //
 // Product: x y = 2^{e_x + e_y} sum_{i,j} A_i B_j.  All products of one group
 // g = i + j carry the same weight, and their sum over K is an integer
@@ -59,6 +63,9 @@ void ozaki_params(int K, int* bits, int* slices) {
 
 bool gemm_ozaki_supported(int n, int K) { return n >= 1 && K >= kOzKBlk && K % kOzKBlk == 0 && K <= 1024; }
 
+// 2^p for -126 <= p <= 127, from its exponent bits.
+__device__ __forceinline__ float pow2f(int p) { return __int_as_float((127 + p) << 23); }
+
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_ozaki_split(const double* src, int64_t rows, int K, int slices, int bits,
                                                      __nv_bfloat16* dst, int* expo) {
@@ -66,22 +73,40 @@ __global__ void __launch_bounds__(256) k_ozaki_split(const double* src, int64_t 
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (row >= rows) return;
   const double* x = src + row * K;
-  double m = 0.0;
-  for (int k = lane; k < K; k += 32) m = fmax(m, fabs(x[k]));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  int e = 0;
-  if (m > 0.0) frexp(m, &e);                   // m = f 2^e, f in [0.5, 1)
+  // largest magnitude: the bit patterns of non-negative doubles order like their values
+  long long mb = 0;
+  for (int k = lane; k < K; k += 32) mb = max(mb, __double_as_longlong(x[k]) & 0x7FFFFFFFFFFFFFFFll);
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  // e with max = f 2^e, f in [0.5, 1): every |x| < 2^e
+  int e = (int)(mb >> 52) - 1022;
+  if ((mb >> 52) == 0) {
+    e = 0;
+    if (mb != 0) frexp(__longlong_as_double(mb), &e);   // subnormal largest value
+  }
   if (lane == 0) expo[row] = e;
   const size_t plane = (size_t)rows * K;
-  const double step = (double)(1 << bits);
+  const int P = (bits - 1) + bits * (slices - 1);   // fraction bits kept (55)
   for (int k = lane; k < K; k += 32) {
-    double t = ldexp(x[k], bits - 1 - e);      // |t| < 2^{b-1}
+    // |x| 2^{P-e} as an integer, rounded to nearest: x = q 2^{E-52}, q the
+    // 53-bit significand, so the value is q 2^{E-52+P-e} with E <= e-1
+    const long long bitsx = __double_as_longlong(x[k]);
+    const int be = (int)((bitsx >> 52) & 0x7ff);
+    const long long q = (bitsx & 0xFFFFFFFFFFFFFll) | (be ? (1ll << 52) : 0ll);
+    const int sh = (be ? be - 1075 : -1074) + P - e;
+    long long F;
+    if (sh >= 0) F = q << sh;                   // sh <= P - 53 (= 2)
+    else if (sh > -62) F = (q + (1ll << (-sh - 1))) >> (-sh);
+    else F = 0;
+    if (bitsx < 0) F = -F;
+    // signed digits from the bottom: d in [-2^{b-1}, 2^{b-1}), the top one the rest
     __nv_bfloat16* o = dst + (size_t)row * K + k;
-    for (int i = 0; i < slices; ++i) {
-      const double a = rint(t);
-      t = (t - a) * step;
-      o[(size_t)i * plane] = __double2bfloat16(ldexp(a, -(bits - 1) - bits * i));
+    const long long half = 1ll << (bits - 1), mask = (1ll << bits) - 1;
+    for (int i = slices - 1; i >= 1; --i) {
+      const long long d = ((F + half) & mask) - half;
+      F = (F - d) >> bits;
+      o[(size_t)i * plane] = __float2bfloat16_rn((float)d * pow2f(-(bits - 1) - bits * i));
     }
+    o[0] = __float2bfloat16_rn((float)F * pow2f(-(bits - 1)));
   }
 }
 

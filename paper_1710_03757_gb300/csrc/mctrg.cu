@@ -161,6 +161,16 @@ extern "C" int mctrg_reset_kernel_stats(mctrg_ctx_t c) {
   return MCTRG_OK;
 }
 
+size_t mctrg_ctx::held_bytes() const {
+  const DevBuf* all[] = {&T0, &shM, &shW, &shSig, &shPerm, &shNnz, &shLns1, &shU, &shH, &Hbuf[0], &Hbuf[1],
+                         &Mb, &Wb, &Xb, &Yb, &sigb, &permb, &nnzb, &ilns1, &iflags, &lnacc, &tflags,
+                         &scratch, &o_lnabs, &o_sign, &o_flags, &o_tflags, &stats, &tcXh, &tcYh, &tcXl,
+                         &tcYl, &tcScale, &tcErr, &ozExp, &bdb, &keptb, &sigtb, &nkb, &vrowsb, &bdscr};
+  size_t b = 0;
+  for (const DevBuf* d : all) b += d->bytes;
+  return b;
+}
+
 void mctrg_ctx::release_all() {
   resolve_events();
   for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
@@ -288,11 +298,15 @@ int mctrg_ctx::init_from_device_tensor(int D0, int L_, int chi_) {
 }
 
 // SVD route of a level whose n x n matrices are X Yt^T with inner dimension K.
-bool mctrg_ctx::use_bidiag(int n, int K) const {
-  if (opt.svd == MCTRG_SVD_JACOBI || n > 1024) return false;
-  if (opt.svd == MCTRG_SVD_BIDIAG) return n >= 2;
+namespace mctrg {
+bool route_bidiag(const mctrg_options& o, int n, int K) {
+  if (o.svd == MCTRG_SVD_JACOBI || n > 1024) return false;
+  if (o.svd == MCTRG_SVD_BIDIAG) return n >= 2;
   return n >= 64 && 2 * K >= n;
 }
+}  // namespace mctrg
+
+bool mctrg_ctx::use_bidiag(int n, int K) const { return route_bidiag(opt, n, K); }
 
 static bool is_pow2(int L) { return L >= 2 && (L & (L - 1)) == 0; }
 
@@ -344,10 +358,18 @@ static size_t tc_operand_bytes(int prec, int n, int d2) {
   }
 }
 
-// Memory plan: bytes per trajectory of a chunk, and bytes per in-flight item.
-void mctrg_ctx::plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& total) const {
+namespace mctrg {
+// Memory plan of a run of n_samples trajectories over levels s0 .. nlev-1 of
+// lv (sampled; the shared prefix is held separately): B trajectories per
+// chunk, S items per sub-batch, and the device bytes the run holds.  At most
+// a quarter of the budget holds the per-item working set (and no more items
+// than a level of one chunk has), the rest the trajectories of a chunk.
+// B < 1 means that not even one trajectory fits.
+void plan_run(const std::vector<LevelInfo>& lv, int s0, int nlev, int chi, const mctrg_options& opt,
+              size_t budget, int64_t n_samples, int64_t& B, int64_t& S, size_t& total) {
   size_t per_traj = 2 * sizeof(double) + sizeof(uint32_t);   // lnacc, tflags
   size_t max_pair = 0, max_items = 0, per_item = 0, bd_scr = 0;
+  int64_t maxN = 1;
   for (int k = s0; k < nlev; ++k) {
     const LevelInfo& a = lv[k];
     size_t hk = (size_t)a.N * 2 * a.n * a.kc * sizeof(double);
@@ -355,11 +377,12 @@ void mctrg_ctx::plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& t
     max_pair = std::max(max_pair, hk + hp);
     max_items = std::max(max_items, (size_t)a.N);
     if (k > s0) {
+      maxN = std::max<int64_t>(maxN, a.N);
       const size_t d2 = (size_t)lv[k - 1].D * lv[k - 1].D;
       size_t pi = (2 * (size_t)a.n * d2 + (size_t)a.n * a.n + (size_t)a.n_pad * a.n + a.n_pad) * sizeof(double) +
                   (a.n_pad + 1) * sizeof(int) + sizeof(double) + sizeof(uint32_t);
       pi += tc_operand_bytes(opt.precision, a.n, (int)d2);
-      if (use_bidiag(a.n, (int)d2)) {   // d, e, tau; kept values and vectors
+      if (route_bidiag(opt, a.n, (int)d2)) {   // d, e, tau; kept values and vectors
         pi += (3 * (size_t)a.n + 32 + 32 * (size_t)a.n) * sizeof(double) + 33 * sizeof(int);
         bd_scr = std::max(bd_scr, bd_vectors_scratch_doubles(a.n, 1 << 16) * sizeof(double));
       }
@@ -372,16 +395,43 @@ void mctrg_ctx::plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& t
     per_traj += fin;
   }
   per_traj += max_pair + max_items * (sizeof(double) + sizeof(uint32_t));
-  const size_t budget = opt.hbm_budget_bytes;
+  const size_t tables = sample_scratch_doubles(lv[nlev - 1].n, chi, 1024) * sizeof(double) + bd_scr;
+  const int64_t Bmax = opt.max_chunk > 0 ? std::min<int64_t>(opt.max_chunk, n_samples) : n_samples;
   const size_t work_budget = std::max<size_t>(budget / 4, 1);
   S = per_item ? (int64_t)std::max<size_t>(1, std::min<size_t>(work_budget / per_item, 1 << 16)) : 1;
-  const size_t work = per_item * (size_t)S + sample_scratch_doubles(lv[nlev - 1].n, chi, 1024) * sizeof(double) +
-                      bd_scr;
+  S = std::max<int64_t>(1, std::min<int64_t>(S, Bmax * maxN));   // no more than a level's items
+  const size_t work = per_item * (size_t)S + tables;
   const size_t rest = budget > work ? budget - work : 0;
   B = (int64_t)(rest / std::max<size_t>(per_traj, 1));
-  if (opt.max_chunk > 0) B = std::min<int64_t>(B, opt.max_chunk);
-  B = std::min<int64_t>(B, n_samples);
+  B = std::min<int64_t>(B, Bmax);
   total = work + (size_t)std::max<int64_t>(B, 1) * per_traj + (size_t)n_samples * 14;
+}
+
+// The same plan for a lattice not yet set up, from the largest leg dimensions
+// its levels can have (D' = min(chi, D^2) from D0, sampling from the first
+// level with D^2 > chi): an upper bound of what plan_run gives after
+// mctrg_init_*, where ranks can only be smaller and exact levels longer.
+void plan_run_bound(int L, int chi, int D0, const mctrg_options& opt, size_t budget, int64_t n_samples,
+                    int64_t& B, int64_t& S, size_t& total) {
+  int m = 0;
+  while ((1 << m) < L) ++m;
+  const int nlev = 2 * m;
+  std::vector<LevelInfo> lv;
+  int D = D0, s0 = nlev;
+  for (int k = 0; k < nlev; ++k) {
+    const int n = D * D;
+    const int kc = std::min(chi, n);
+    lv.push_back(LevelInfo{level_count(L, k), D, n, n + (n & 1), kc});
+    if (s0 == nlev && n > chi && k >= opt.deterministic_levels) s0 = k;
+    D = kc;
+  }
+  if (s0 == nlev) { B = n_samples; S = 1; total = (size_t)n_samples * 14; return; }
+  plan_run(lv, s0, nlev, chi, opt, budget, n_samples, B, S, total);
+}
+}  // namespace mctrg
+
+void mctrg_ctx::plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& total) const {
+  plan_run(lv, s0, nlev, chi, opt, opt.hbm_budget_bytes, n_samples, B, S, total);
 }
 
 extern "C" int mctrg_footprint(mctrg_ctx_t c, int64_t n_samples, size_t* bytes) {

@@ -27,6 +27,12 @@ struct LevelInfo {
   int D, n, n_pad, kc;
 };
 
+bool route_bidiag(const mctrg_options& o, int n, int K);
+void plan_run(const std::vector<LevelInfo>& lv, int s0, int nlev, int chi, const mctrg_options& opt,
+              size_t budget, int64_t n_samples, int64_t& B, int64_t& S, size_t& total);
+void plan_run_bound(int L, int chi, int D0, const mctrg_options& opt, size_t budget, int64_t n_samples,
+                    int64_t& B, int64_t& S, size_t& total);
+
 void set_last_cuda_error(cudaError_t e);
 const char* last_message();
 void finish_estimate(mctrg_estimate* e);
@@ -89,4 +95,5 @@ struct mctrg_ctx {
           mctrg_estimate* est);
   bool any_noconv(int64_t n);
   void release_all();
+  size_t held_bytes() const;   // device bytes the context's buffers hold now
 };

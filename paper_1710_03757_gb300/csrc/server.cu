@@ -1,16 +1,23 @@
 // Serving loop: continuous batching of Monte Carlo TRG estimate jobs.
 //
 // Jobs (beta, h, L, chi, target standard error of ln Z) arrive at any time.
-// A fixed pool of workers, each with its own CUDA stream and a persistent
-// context holding an equal share of the device-memory budget, takes queued
-// jobs in arrival order as soon as a worker is free; a job advances in rounds
-// of trajectories (chunked to fit its worker's memory), so the kernels of all
-// running jobs share the device concurrently, and a worker that finishes a
-// job immediately starts the next queued one with the buffers it already
-// holds.  A job's
-// trajectory i always uses Philox counter i under the job's seed and its
-// rounds merge through the sufficient statistics of mctrg_merge_estimates,
-// so its result is the same alone and in any mix.
+// A pool of workers (slots), each with its own CUDA stream and a persistent
+// context, takes queued jobs as soon as a slot is free AND the job's device
+// footprint fits the memory the server has not yet handed out: admission by
+// HBM footprint.  A job's footprint is the memory plan of its largest round
+// (the same planner mctrg_footprint reports, from the largest leg dimensions
+// the lattice can have, so it bounds what the context allocates); a worker
+// keeps the buffers of the jobs it ran (cudaFree would wait for the whole
+// device and serialize every running job) and counts them against the
+// budget, and idle workers give theirs back only when a queued job is blocked
+// on memory.  A job advances in rounds of trajectories, so the kernels of
+// all running jobs share the device on their streams; after each round the
+// standard error of ln Z is projected to max_samples by the 1/sqrt(N) law
+// (Sec. V, Eq. shrunkDev) and a job that cannot reach its target stops with
+// EUNREACHABLE.  A job's trajectory i always uses Philox counter i under the
+// job's seed and its rounds merge through the sufficient statistics of
+// mctrg_merge_estimates, so its result is the same alone and in any mix.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -20,6 +27,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <vector>
 
 #include "../../include/mctrg.h"
 #include "mctrg_internal.h"
@@ -32,47 +40,35 @@ struct Job {
   uint64_t id = 0;
   double beta = 0, h = 0, target = 0;
   int L = 0, chi = 0;
-  int64_t max_samples = 0;
+  int64_t max_samples = 0, round0 = 0;
   uint64_t seed = 0;
-  size_t footprint = 0;
+  size_t footprint = 0;     // device bytes of the largest round (plan bound)
+  int passed_over = 0;      // times a later job was admitted while this one waited for memory
   Clock::time_point t_submit, t_done;
   int state = 0;            // 0 queued, 1 running, 2 done
   int status = MCTRG_OK;
   mctrg_estimate est{};
 };
 
-// Upper bound of the device bytes of a job that runs rounds of R trajectories:
-// leg dimensions grow as D' = min(chi, D^2) from D = 2.
-size_t job_footprint(int L, int chi, int64_t R) {
-  int m = 0;
-  while ((1 << m) < L) ++m;
-  const int nlev = 2 * m;
-  int D = 2;
-  size_t per_traj = 64, work = 0, maxpair = 0, prevh = 0;
-  for (int k = 0; k < nlev; ++k) {
-    const size_t n = (size_t)D * D;
-    const int kc = (int)std::min<size_t>((size_t)chi, n);
-    const size_t N = ((size_t)L * L) >> k;
-    const size_t hk = N * 2 * n * kc * 8;
-    maxpair = std::max(maxpair, hk + prevh);
-    prevh = hk;
-    work = std::max(work, (size_t)(5 * n * n * 8 + (n + 1) * 65 * 8));
-    D = kc;
-  }
-  per_traj += maxpair;
-  // trajectories in flight, one matrix of working space, fixed buffers
-  return per_traj * (size_t)R + work + (64u << 20);
-}
+struct Worker {
+  mctrg_ctx_t ctx = nullptr;
+  size_t held = 0;          // bytes counted against the budget for this worker
+  bool release = false;     // give the buffers back before the next job
+};
+
+constexpr int64_t kRoundMax = 8192;   // rounds double from the first up to this
+constexpr int kMaxPassOver = 32;      // then the oldest job blocks the queue until memory frees
 
 }  // namespace
 
 struct mctrg_server {
   mctrg_options opt{};
-  size_t budget = 0;                // whole server
-  size_t worker_budget = 0;         // each worker context
+  size_t budget = 0;                // device bytes the server may hand out
+  size_t reserved = 0;              // sum of the workers' held bytes
   int n_workers = 16;
+  std::vector<Worker> w;
   std::mutex mu;
-  std::condition_variable cv;       // workers wake on submit / stop
+  std::condition_variable cv;       // workers wake on submit / stop / memory released
   std::condition_variable done_cv;  // waiters wake when a job finishes
   std::deque<Job*> queue;
   std::map<uint64_t, Job*> jobs;
@@ -81,16 +77,36 @@ struct mctrg_server {
   uint64_t next_id = 1;
   std::vector<std::thread> workers;
 
-  static constexpr int64_t kRound0 = 256;   // first round; later rounds double up to kRoundMax
-  static constexpr int64_t kRoundMax = 8192;
+  // Under mu: the queued job worker wi may take now, or null.  The oldest job
+  // that fits (its footprint beyond what the worker already holds, within the
+  // unreserved budget); a job passed over kMaxPassOver times stops the others.
+  Job* admit(int wi) {
+    const size_t free_b = budget > reserved ? budget - reserved : 0;
+    for (auto it = queue.begin(); it != queue.end(); ++it) {
+      Job* j = *it;
+      const size_t need = j->footprint > w[wi].held ? j->footprint - w[wi].held : 0;
+      if (need <= free_b) {
+        for (auto q = queue.begin(); q != it; ++q) ++(*q)->passed_over;
+        reserved += need;
+        w[wi].held += need;
+        queue.erase(it);
+        return j;
+      }
+      if (j->passed_over >= kMaxPassOver) break;
+    }
+    // the oldest job is blocked on memory: idle workers give their buffers back
+    if (!queue.empty() && w[wi].held > 0) w[wi].release = true;
+    return nullptr;
+  }
 
   // One job on a worker's persistent context: rounds of trajectories until the
-  // target standard error of ln Z or max_samples is reached.
+  // target standard error of ln Z is reached, projected out of reach, or
+  // max_samples is spent.
   void run_job(mctrg_ctx_t ctx, Job* j) {
     int status = mctrg_init_lattice(ctx, j->beta, j->h, j->L, j->chi);
     mctrg_estimate total{};
-    bool have = false;
-    int64_t done = 0, round = kRound0;
+    bool have = false, reached = false;
+    int64_t done = 0, round = j->round0;
     while (status == MCTRG_OK && done < j->max_samples) {
       if (stop_flag.load(std::memory_order_relaxed)) break;   // server shutting down
       const int64_t R = std::min(round, j->max_samples - done);
@@ -103,11 +119,15 @@ struct mctrg_server {
         mctrg_merge_estimates(parts, 2, &total);
       }
       done += R;
-      if (total.status == MCTRG_OK && total.se_ln_Z <= j->target) break;
+      if (total.status == MCTRG_OK && total.se_ln_Z <= j->target) { reached = true; break; }
+      // projection of the standard error to max_samples (1/sqrt(N)); a margin
+      // of 2 absorbs the scatter of an early estimate of it
+      if (total.status == MCTRG_OK && total.n >= std::min<int64_t>(64, j->round0) && std::isfinite(total.se_ln_Z) &&
+          total.se_ln_Z * std::sqrt((double)total.n / (double)j->max_samples) > 2.0 * j->target)
+        break;
       round = std::min(round * 2, kRoundMax);
     }
-    if (status == MCTRG_OK && !(total.status == MCTRG_OK && total.se_ln_Z <= j->target))
-      status = MCTRG_EUNREACHABLE;
+    if (status == MCTRG_OK && !reached) status = MCTRG_EUNREACHABLE;
     std::lock_guard<std::mutex> lk(mu);
     j->est = total;
     j->status = status;
@@ -116,39 +136,63 @@ struct mctrg_server {
     done_cv.notify_all();
   }
 
-  // A worker owns one stream and one context for its whole life, so jobs reuse
-  // device buffers instead of allocating and freeing them (cudaFree waits for
-  // the whole device, which would serialize every running job).
-  void worker_loop() {
+  void finish_failed(Job* j, int status) {
+    std::lock_guard<std::mutex> lk(mu);
+    j->status = status;
+    j->t_done = Clock::now();
+    j->state = 2;
+    done_cv.notify_all();
+  }
+
+  void worker_loop(int wi) {
     cudaSetDevice(opt.device);
     cudaStream_t st = nullptr;
     mctrg_ctx_t ctx = nullptr;
+    mctrg_options o = opt;
+    o.profile = 0;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) {
-      mctrg_options o = opt;
       o.cuda_stream = st;
-      o.hbm_budget_bytes = worker_budget;
-      o.profile = 0;
+      o.hbm_budget_bytes = budget;
       if (mctrg_create(&o, &ctx) != MCTRG_OK) ctx = nullptr;
     }
     for (;;) {
       Job* j = nullptr;
+      bool release = false;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv.wait(lk, [&] { return stop || !queue.empty(); });
+        cv.wait(lk, [&] {
+          if (stop) return true;
+          if (queue.empty()) return false;
+          j = admit(wi);
+          return j != nullptr || w[wi].release;
+        });
         if (stop) break;
-        j = queue.front();
-        queue.pop_front();
-        j->state = 1;
+        if (!j) {                      // give the buffers back, then try again
+          release = true;
+          w[wi].release = false;
+        } else {
+          j->state = 1;
+        }
       }
-      if (ctx) {
-        run_job(ctx, j);
-      } else {
+      if (release) {
+        if (ctx) ctx->release_all();
         std::lock_guard<std::mutex> lk(mu);
-        j->status = MCTRG_ECUDA;
-        j->t_done = Clock::now();
-        j->state = 2;
-        done_cv.notify_all();
+        reserved -= w[wi].held;
+        w[wi].held = 0;
+        cv.notify_all();
+        continue;
       }
+      if (!ctx) { finish_failed(j, MCTRG_ECUDA); continue; }
+      // the context plans its chunks within what this worker holds
+      ctx->opt.hbm_budget_bytes = w[wi].held;
+      run_job(ctx, j);
+      std::lock_guard<std::mutex> lk(mu);
+      const size_t actual = ctx->held_bytes();
+      if (actual > w[wi].held) {       // the plan bound is exceeded only by the shared prefix
+        reserved += actual - w[wi].held;
+        w[wi].held = actual;
+      }
+      cv.notify_all();
     }
     if (ctx) mctrg_destroy(ctx);
     if (st) cudaStreamDestroy(st);
@@ -157,6 +201,8 @@ struct mctrg_server {
 
 extern "C" int mctrg_server_create(const mctrg_options* opt, mctrg_server_t* out) {
   if (!opt || !out) return MCTRG_EINVAL;
+  if (opt->precision < MCTRG_FP64 || opt->precision > MCTRG_FP64TC || opt->deterministic_levels < 0)
+    return MCTRG_EINVAL;
   *out = nullptr;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) return MCTRG_ECUDA;
@@ -170,8 +216,8 @@ extern "C" int mctrg_server_create(const mctrg_options* opt, mctrg_server_t* out
     s->opt.hbm_budget_bytes = (size_t)(0.8 * (double)fr);
   }
   s->budget = s->opt.hbm_budget_bytes;
-  s->worker_budget = s->budget / (size_t)s->n_workers;
-  for (int w = 0; w < s->n_workers; ++w) s->workers.emplace_back(&mctrg_server::worker_loop, s);
+  s->w.resize(s->n_workers);
+  for (int i = 0; i < s->n_workers; ++i) s->workers.emplace_back(&mctrg_server::worker_loop, s, i);
   *out = s;
   return MCTRG_OK;
 }
@@ -187,13 +233,21 @@ extern "C" int mctrg_server_submit(mctrg_server_t s, double beta, double h, int 
   Job* j = new Job();
   j->beta = beta; j->h = h; j->L = L; j->chi = chi; j->target = target_se_lnZ;
   j->max_samples = max_samples; j->seed = seed;
-  // a job runs in chunks that fit a worker's share of the memory; if even one
-  // trajectory cannot fit there, it can never run
-  j->footprint = job_footprint(L, chi, 1);
-  if (j->footprint > s->worker_budget) {
+  j->round0 = L <= 64 ? 256 : (L <= 256 ? 32 : 4);
+  // footprint of the largest round within half the budget (so that other jobs
+  // run beside it); a job of which not even one trajectory fits the whole
+  // budget can never run
+  const int64_t Rmax = std::min<int64_t>(max_samples, kRoundMax);
+  int64_t B = 0, S = 0;
+  size_t total = 0;
+  mctrg::plan_run_bound(L, chi, 2, s->opt, s->budget, 1, B, S, total);
+  if (B < 1) {
     delete j;
     return MCTRG_EUNREACHABLE;
   }
+  mctrg::plan_run_bound(L, chi, 2, s->opt, s->budget / 2, Rmax, B, S, total);
+  if (B < 1) mctrg::plan_run_bound(L, chi, 2, s->opt, s->budget, Rmax, B, S, total);
+  j->footprint = total;
   j->t_submit = Clock::now();
   std::lock_guard<std::mutex> lk(s->mu);
   j->id = s->next_id++;
@@ -242,6 +296,29 @@ extern "C" int mctrg_server_wait(mctrg_server_t s, uint64_t job_id, double timeo
   }
 }
 
+extern "C" int mctrg_server_footprint(mctrg_server_t s, int L, int chi, int64_t max_samples, size_t* bytes) {
+  if (!s || !bytes || L < 2 || (L & (L - 1)) || L > 65536 || chi < 1 || chi > 32 || max_samples < 1)
+    return MCTRG_EINVAL;
+  int64_t B = 0, S = 0;
+  size_t total = 0;
+  mctrg::plan_run_bound(L, chi, 2, s->opt, s->budget, 1, B, S, total);
+  if (B < 1) return MCTRG_EUNREACHABLE;
+  mctrg::plan_run_bound(L, chi, 2, s->opt, s->budget / 2, std::min<int64_t>(max_samples, kRoundMax), B, S,
+                        total);
+  if (B < 1)
+    mctrg::plan_run_bound(L, chi, 2, s->opt, s->budget, std::min<int64_t>(max_samples, kRoundMax), B, S, total);
+  *bytes = total;
+  return MCTRG_OK;
+}
+
+extern "C" int mctrg_server_memory(mctrg_server_t s, size_t* budget, size_t* reserved) {
+  if (!s) return MCTRG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (budget) *budget = s->budget;
+  if (reserved) *reserved = s->reserved;
+  return MCTRG_OK;
+}
+
 extern "C" void mctrg_server_destroy(mctrg_server_t s) {
   if (!s) return;
   {
@@ -254,7 +331,7 @@ extern "C" void mctrg_server_destroy(mctrg_server_t s) {
     s->cv.notify_all();
   }
   for (std::thread& t : s->workers)
-    if (t.joinable()) t.join();   // running jobs finish their current job first
+    if (t.joinable()) t.join();   // running jobs finish their current round first
   for (auto& kv : s->jobs) delete kv.second;
   s->jobs.clear();
   delete s;

@@ -24,6 +24,7 @@ EXPORTS = [
     "mctrg_server_destroy", "mctrg_plan_level", "mctrg_philox_uniform", "mctrg_kernel_stats",
     "mctrg_reset_kernel_stats", "mctrg_svd_batched", "mctrg_svd_batched_noalloc",
     "mctrg_svd_bidiag_batched", "mctrg_measure_fp64_peak", "mctrg_contract_batched",
+    "mctrg_server_footprint", "mctrg_server_memory",
 ]
 K_FORM_XY, K_GEMM, K_JACOBI, K_SAMPLE, K_TRACE, K_OTHER, K_BIDIAG, K_BISECT, K_VECTORS, K_COUNT = range(10)
 KERNEL_NAMES = ["form_xy", "gemm", "jacobi", "sample_split", "trace", "other", "bidiag", "bisect", "vectors"]
@@ -84,6 +85,8 @@ def lib():
             "mctrg_server_wait": (c_int, [vp, u64, c_double, ctypes.POINTER(Estimate),
                                           ctypes.POINTER(c_double)]),
             "mctrg_server_destroy": (None, [vp]),
+            "mctrg_server_footprint": (c_int, [vp, c_int, c_int, i64, ctypes.POINTER(ctypes.c_size_t)]),
+            "mctrg_server_memory": (c_int, [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
             "mctrg_plan_level": (c_int, [c_int, c_int, vp, vp]),
             "mctrg_philox_uniform": (c_double, [u64, u32, u32, u32, u32]),
             "mctrg_kernel_stats": (c_int, [vp, c_int, ctypes.POINTER(KernelStat)]),
@@ -285,6 +288,20 @@ def mctrg_server_wait(srv, job_id, timeout_s):
     est, lat = Estimate(), ctypes.c_double()
     s = lib().mctrg_server_wait(srv, int(job_id), float(timeout_s), ctypes.byref(est), ctypes.byref(lat))
     return s, est, lat.value
+
+
+def mctrg_server_footprint(srv, L, chi, max_samples):
+    """(status, bytes) a job would be admitted with."""
+    b = ctypes.c_size_t()
+    s = lib().mctrg_server_footprint(srv, int(L), int(chi), int(max_samples), ctypes.byref(b))
+    return s, b.value
+
+
+def mctrg_server_memory(srv):
+    """(budget, reserved) device bytes of the server."""
+    b, r = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().mctrg_server_memory(srv, ctypes.byref(b), ctypes.byref(r)), "mctrg_server_memory")
+    return b.value, r.value
 
 
 def mctrg_server_destroy(srv):

@@ -1,8 +1,10 @@
 """Serving loop: continuous batching of estimate jobs (mctrg_server_*).
 
-Jobs that arrive while others run are admitted as device memory frees up and
-run concurrently on their own streams; each job's trajectories use its own
-counters, so its result must be the same alone and in any mix."""
+Jobs that arrive while others run are admitted by device footprint as slots
+and memory free up, and run concurrently on their own streams; each job's
+trajectories use its own counters, so its result must be the same alone and
+in any mix.  A job whose standard error, projected by 1/sqrt(N) (Sec. V, Eq.
+shrunkDev), cannot reach its target within max_samples stops early."""
 import math
 import time
 
@@ -92,11 +94,81 @@ def test_status_codes():
         assert st == 0
         assert mctrg.mctrg_server_poll(srv, j)[0] == mctrg.MCTRG_EAGAIN
         assert mctrg.mctrg_server_wait(srv, j, 0.01)[0] == mctrg.MCTRG_ETIMEDOUT
-        # a target that max_samples cannot reach: result returned, status says so
+        # a target that max_samples cannot reach: projected after the first
+        # round (256 trajectories), result returned, status says so
         st, est, lat = mctrg.mctrg_server_wait(srv, j, 300.0)
-        assert st == mctrg.MCTRG_EUNREACHABLE and est.n == 1 << 12
+        assert st == mctrg.MCTRG_EUNREACHABLE and est.n == 256
         # destroying the server with a job still running is clean
         st, j2 = mctrg.mctrg_server_submit(srv, 0.44, 0.0, 32, 16, 1e-9, 1 << 14, 4)
         assert st == 0
+    finally:
+        mctrg.mctrg_server_destroy(srv)
+
+
+def test_admission_by_footprint():
+    # a budget of three jobs' footprints: the workers never hold more than the
+    # budget (plus the shared-prefix buffers a plan does not count), all jobs
+    # finish, and each equals its run on a server with room to spare
+    job = lambda k: (0.3 + 0.02 * k, 0.0, 16, 8, 1e-9, 1 << 12, 900 + k)
+    roomy = mctrg.mctrg_server_create()
+    try:
+        st, fp = mctrg.mctrg_server_footprint(roomy, 16, 8, 1 << 12)
+        assert st == 0 and fp > 0
+        ref = {}
+        for k in range(8):
+            st, j = mctrg.mctrg_server_submit(roomy, *job(k))
+            ref[k] = j
+        ref = {k: mctrg.mctrg_server_wait(roomy, j, 300.0)[1] for k, j in ref.items()}
+    finally:
+        mctrg.mctrg_server_destroy(roomy)
+    budget = 3 * fp + fp // 2
+    srv = mctrg.mctrg_server_create(mctrg.make_options(hbm_budget_bytes=budget))
+    try:
+        ids = {}
+        for k in range(8):
+            st, j = mctrg.mctrg_server_submit(srv, *job(k))
+            assert st == 0
+            ids[k] = j
+        import threading
+        peak, done = [0], threading.Event()
+
+        def watch():
+            while not done.is_set():
+                b, r = mctrg.mctrg_server_memory(srv)
+                assert b == budget
+                peak[0] = max(peak[0], r)
+                time.sleep(0.002)
+        th = threading.Thread(target=watch)
+        th.start()
+        try:
+            res = _wait_all(srv, list(ids.values()))
+        finally:
+            done.set()
+            th.join()
+    finally:
+        mctrg.mctrg_server_destroy(srv)
+    print("budget %d, peak held %d (footprint %d)" % (budget, peak[0], fp))
+    assert 0 < peak[0] <= budget + (64 << 20)
+    for k, j in ids.items():
+        st, est, _ = res[j]
+        assert st == mctrg.MCTRG_EUNREACHABLE
+        assert est.n == ref[k].n and est.sum_x == ref[k].sum_x and est.m2_x == ref[k].m2_x
+
+
+def test_literal_configurations_are_refused_fast():
+    srv = mctrg.mctrg_server_create()
+    try:
+        t = time.time()
+        # far beyond the device: refused at submission
+        for L, chi in ((65536, 8), (4096, 32), (16384, 16)):
+            assert mctrg.mctrg_server_submit(srv, 0.44, 0.0, L, chi, 1e-5, 1 << 18, 1)[0] == mctrg.MCTRG_EUNREACHABLE
+        assert mctrg.mctrg_server_footprint(srv, 4096, 32, 1 << 18)[0] == mctrg.MCTRG_EUNREACHABLE
+        # feasible lattices with targets far out of reach: stopped after the first round
+        ids = [mctrg.mctrg_server_submit(srv, 0.44, 0.0, L, chi, tgt, 1 << 18, 2)[1]
+               for L, chi, tgt in ((256, 8, 1e-5), (512, 8, 1e-6), (256, 16, 1e-6))]
+        for j in ids:
+            st, est, lat = mctrg.mctrg_server_wait(srv, j, 600.0)
+            assert st == mctrg.MCTRG_EUNREACHABLE and est.n <= 32
+        print("literal jobs refused or projected out of reach in %.1f s" % (time.time() - t))
     finally:
         mctrg.mctrg_server_destroy(srv)
