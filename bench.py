@@ -139,10 +139,15 @@ def oracle_rate(wl, seconds_budget=20.0, workers=None):
     return rate, workers, desc
 
 
+# the serving stand-in's sample cap: 2^16 (the literal workload's 2^18 would hold one job for
+# minutes at these lattice sizes and keep the bench's serving phase from ending in a few minutes)
+SERVE_MAX_SAMPLES = 1 << 16
+
+
 def _serve_mix(rng):
     """One job of the serving stand-in (small lattices; the literal sizes run as refusals)."""
     return (float(rng.uniform(0.3, 0.6)), float(rng.choice([0.0, 0.05])), int(rng.choice([4, 8, 16, 32])),
-            int(rng.choice([2, 4, 8])), float(10 ** rng.uniform(-4, -2)), 1 << 18, int(rng.integers(1 << 62)))
+            int(rng.choice([2, 4, 8])), float(10 ** rng.uniform(-4, -2)), SERVE_MAX_SAMPLES, int(rng.integers(1 << 62)))
 
 
 def _serve_literal(rng):
@@ -152,17 +157,17 @@ def _serve_literal(rng):
             int(rng.choice([8, 16, 32])), float(10 ** rng.uniform(-6, -4)), 1 << 18, int(rng.integers(1 << 62)))
 
 
-def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_every=20, drain_s=240.0):
+def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_every=10, drain_s=120.0, burst_jobs=16):
     """Continuous batching under Poisson arrivals at a stated fraction of capacity.
 
     Job mix (small-lattice stand-in of the serving workload): beta uniform in
     [0.3, 0.6], h in {0, 0.05}, L in {4, 8, 16, 32}, chi in {2, 4, 8}, target
-    standard error of ln Z log-uniform in [1e-4, 1e-2], at most 2^18
+    standard error of ln Z log-uniform in [1e-4, 1e-2], at most 2^16
     trajectories; every `literal_every`-th arrival is a job at the literal
     sizes, which must be refused at submission (footprint beyond the device)
     or stopped after its first round (target projected out of reach).  The
     server's capacity (trajectories/s and trajectories per job) is measured
-    first on a burst of 48 jobs from the mix; arrivals then come at `load`
+    first on a burst of `burst_jobs` jobs from the mix; arrivals then come at `load`
     times the job rate that capacity sustains.  Jobs still running `drain_s`
     after the last arrival are reported as unfinished.
     """
@@ -171,10 +176,10 @@ def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_every=20,
     srv = mctrg.mctrg_server_create()
     try:
         t0 = time.perf_counter()
-        burst = [mctrg.mctrg_server_submit(srv, *_serve_mix(rng))[1] for _ in range(48)]
+        burst = [mctrg.mctrg_server_submit(srv, *_serve_mix(rng))[1] for _ in range(burst_jobs)]
         traj = sum(mctrg.mctrg_server_wait(srv, j, 900.0)[1].n for j in burst)
         cap = traj / (time.perf_counter() - t0)
-        rate = load * cap / (traj / 48.0)
+        rate = load * cap / (traj / float(burst_jobs))
         ids, lit, refused, n_arr = [], [], 0, 0
         t0 = time.perf_counter()
         t_next = 0.0
@@ -223,7 +228,7 @@ def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_every=20,
             "literal_jobs": {"refused_at_submit": refused, "projected_out_of_reach": len(lit),
                              "latency_max_s": max(lit_lat) if lit_lat else None},
             "mix": "beta U[0.3,0.6], h {0,0.05}, L {4,8,16,32}, chi {2,4,8}, target SE(ln Z) 1e-4..1e-2 "
-                   "log-uniform, max 2^18 trajectories; every %dth arrival at the literal sizes (L 2^8..2^16, "
+                   "log-uniform, max 2^16 trajectories; every %dth arrival at the literal sizes (L 2^8..2^16, "
                    "chi {8,16,32}, target 1e-6..1e-4)" % literal_every}
 
 
@@ -325,9 +330,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--traj-per-step", type=int, default=0)
+    ap.add_argument("--precision", default="", choices=["", "fp64", "tf32", "bf16", "tf32x3", "bf16x3", "fp64tc"],
+                    help="arithmetic of the contraction (default: the workload's, FP64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--table1", action="store_true",
@@ -336,6 +343,8 @@ def main():
     wl = dict(WORKLOADS[args.workload])
     if args.traj_per_step:
         wl["traj_per_step"] = args.traj_per_step
+    if args.precision:
+        wl["precision"] = ["fp64", "tf32", "bf16", "tf32x3", "bf16x3", "fp64tc"].index(args.precision)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -483,7 +492,8 @@ def main():
     peaks, peak_src = measured_peaks()
     flop_classes = (mctrg.K_BIDIAG, mctrg.K_JACOBI, mctrg.K_VECTORS, mctrg.K_SAMPLE, mctrg.K_FORM_XY,
                     mctrg.K_GEMM, mctrg.K_TRACE)
-    if dom in flop_classes and ds.flops_alg > 0 and wl["precision"] == 0:
+    fp64_dom = dom in flop_classes and (dom != mctrg.K_GEMM or wl["precision"] == 0)
+    if fp64_dom and ds.flops_alg > 0:
         achieved = ds.flops_alg / (ds.ms / 1000.0) / 1e12 if ds.ms > 0 else 0.0
         peak = fp64_peak if pst == 0 and fp64_peak > 0 else FP64_NOMINAL_TFLOPS
         per_matrix = {mctrg.K_JACOBI: JACOBI_DRAM_BYTES_PER_MATRIX_N256,
@@ -510,7 +520,8 @@ def main():
     line = {"metric": "trajectories/s", "value": value, "unit": "trajectories/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": ["f64", "f64+tf32", "f64+bf16"][wl["precision"]], "data": "synthetic",
+            "dtype": ["f64", "f64+tf32", "f64+bf16", "f64+tf32x3", "f64+bf16x3", "f64 (bf16 slices)"][wl["precision"]],
+            "data": "synthetic",
             "config": {"workload": args.workload, "L": wl["L"], "chi": wl["chi"], "beta": wl["beta"],
                        "h": wl["h"], "trajectories_per_step_per_gpu": B, "parallelism": "replicas%d" % world,
                        "l2": "working set (halves, matrices) far larger than L2; no flush needed"},

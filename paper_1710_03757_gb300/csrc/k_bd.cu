@@ -503,6 +503,10 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
     // the whole range [zero bound, |T|]
     double lo = fmax(tlo, (double)lo32 * (1.0 - 0x1.0p-12));
     double hi = fmin(top, (double)hi32 * (1.0 + 0x1.0p-12));
+    // a bracket already within the tolerance (the small values: their FP32
+    // bracket, a relative 2^-11 wide, is below 2^-51 |T| in absolute terms)
+    // needs no FP64 count: the refinement below would not move it
+    if (hi - lo <= tol) { sg[r] = G * (0.5 * (lo + hi)); continue; }
     double f_lo, f_hi;
     int e_lo, e_hi;
     int c_lo = sturm_eval(oo, n, lo, f_lo, e_lo);
