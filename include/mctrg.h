@@ -313,8 +313,9 @@ int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, double* sigm
  * FP64 arithmetic rate of a device, the peak against which the FP64 kernels
  * (the SVD routes, the FP64 contraction) are quoted: a probe kernel runs, in
  * every thread of a whole number of CTAs per SM, 4, 8 or 16 independent
- * chains of about `steps` fused multiply-adds (x <- x b + c) at 128, 256 and
- * 512 threads per CTA; for each shape one untimed launch, then three launches
+ * chains of about `steps` fused multiply-adds (x <- x b + c), or a 4 x 4
+ * outer product of changing operands per step (16 fused multiply-adds), at
+ * 128, 256 and 512 threads per CTA; for each shape one untimed launch, then three launches
  * timed with CUDA events on the legacy default stream.  *tflops = the best
  * rate (2 flops per step and chain); *ms (may be NULL) receives that launch's
  * duration.  The paper has no counterpart (it reports no timings).

@@ -39,7 +39,8 @@ extern "C" int mctrg_contract_batched(const double* X, const double* Yt, int D, 
     uint32_t herr = 0;
     mctrg::GemmOzArgs ga{};
     ga.M = M; ga.D = D; ga.n = n; ga.K = K; ga.c0 = 0; ga.n_items = batch; ga.Nnew = 1; ga.L = 2;
-    ga.level_new = 0; ga.fixed_parity = 0; ga.expX = ex; ga.expY = ex + rows; ga.slices = slices; ga.err = err;
+    ga.level_new = 0; ga.fixed_parity = 0; ga.expX = ex; ga.expY = ex + rows; ga.slices = slices;
+    ga.bits = bits; ga.err = err;
     if (cudaMemsetAsync(err, 0, sizeof(uint32_t), st) != cudaSuccess ||
         mctrg::launch_ozaki_split(X, rows, K, xs, ex, st) != cudaSuccess ||
         mctrg::launch_ozaki_split(Yt, rows, K, ys, ex + rows, st) != cudaSuccess ||

@@ -66,6 +66,14 @@ bool gemm_ozaki_supported(int n, int K) { return n >= 1 && K >= kOzKBlk && K % k
 // 2^p for -126 <= p <= 127, from its exponent bits.
 __device__ __forceinline__ float pow2f(int p) { return __int_as_float((127 + p) << 23); }
 
+// 2^p as a double for any p (exponent bits in the normal range; beyond it a
+// product of two powers, so underflow and overflow round as a scaling would).
+__device__ __forceinline__ double pow2d(int p) {
+  if (p >= -1022 && p <= 1023) return __hiloint2double((1023 + p) << 20, 0);
+  const int h = p / 2;
+  return __hiloint2double((1023 + h) << 20, 0) * __hiloint2double((1023 + (p - h)) << 20, 0);
+}
+
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_ozaki_split(const double* src, int64_t rows, int K, int slices, int bits,
                                                      __nv_bfloat16* dst, int* expo) {
@@ -100,13 +108,15 @@ __global__ void __launch_bounds__(256) k_ozaki_split(const double* src, int64_t 
     if (bitsx < 0) F = -F;
     // signed digits from the bottom: d in [-2^{b-1}, 2^{b-1}), the top one the rest
     __nv_bfloat16* o = dst + (size_t)row * K + k;
-    const long long half = 1ll << (bits - 1), mask = (1ll << bits) - 1;
+    // (the digit depends only on the low bits of F: 32-bit arithmetic and a
+    // 32-bit conversion, both off the FP64 pipe)
+    const int half = 1 << (bits - 1), mask = (1 << bits) - 1;
     for (int i = slices - 1; i >= 1; --i) {
-      const long long d = ((F + half) & mask) - half;
+      const int d = (int)(((unsigned)(F & 0xffffffffll) + (unsigned)half) & (unsigned)mask) - half;
       F = (F - d) >> bits;
-      o[(size_t)i * plane] = __float2bfloat16_rn((float)d * pow2f(-(bits - 1) - bits * i));
+      o[(size_t)i * plane] = __float2bfloat16_rn(__int2float_rn(d) * pow2f(-(bits - 1) - bits * i));
     }
-    o[0] = __float2bfloat16_rn((float)F * pow2f(-(bits - 1)));
+    o[0] = __float2bfloat16_rn(__int2float_rn((int)F) * pow2f(-(bits - 1)));
   }
 }
 
@@ -196,23 +206,40 @@ __global__ void __launch_bounds__(128, 1)
     const int* ey = a.expY + (int64_t)it * n;
     const int er = r < n ? a.expX[(int64_t)it * n + r] : 0;
     const int al = r / D, be = r - al * D;
+    // group g holds an integer I_g times 2^{-2(b-1)-b g} (exact below 2^24; the
+    // later, larger groups are integers too, at most 2^27): read back as
+    // integers (an FP32 scaling by a power of two and a conversion), packed
+    // into two 64-bit words (groups 0..3 and 4..s-1, each below 2^53), and
+    // only those two are converted to FP64 and scaled by 2^{e_x + e_y}
+    const int bits = a.bits;
+    const int w0 = 2 * (bits - 1);                  // weight exponent of group 0
+    const int split = S < 4 ? S : 4;                 // groups in the first word
     for (int c0 = 0; c0 < kOzTileN; c0 += 32) {
-      double acc[32];
+      long long hi[32], lo[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] = 0.0;
-      for (int g = S - 1; g >= 0; --g) {        // smallest group first
+      for (int j = 0; j < 32; ++j) { hi[j] = 0; lo[j] = 0; }
+      for (int g = 0; g < S; ++g) {
         uint32_t v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * kOzTileN + c0), v);
+        const float up = pow2f(w0 + bits * g);
+        if (g < split) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] += (double)__uint_as_float(v[j]);
+          for (int j = 0; j < 32; ++j) hi[j] = (hi[j] << bits) + __float2int_rn(__uint_as_float(v[j]) * up);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) lo[j] = (lo[j] << bits) + __float2int_rn(__uint_as_float(v[j]) * up);
+        }
       }
       if (r < n) {
+        // value = hi 2^{-w0 - b (split-1)} + lo 2^{-w0 - b (S-1)}, times 2^{er + ec}
+        const int ph = -w0 - bits * (split - 1) + er, pl = -w0 - bits * (S - 1) + er;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int cc = nt * kOzTileN + c0 + j;
           if (cc < n) {
             const int de = cc / D, ga = cc - de * D;
-            const double val = scalbn(acc[j], er + ey[cc]);
+            const int ec = ey[cc];
+            const double val = fma((double)hi[j], pow2d(ph + ec), (double)lo[j] * pow2d(pl + ec));
             if (par == 0) Mo[(int64_t)r * n + cc] = val;
             else Mo[(int64_t)(be * D + de) * n + (ga * D + al)] = val;
           }
@@ -258,6 +285,9 @@ cudaError_t launch_gemm_ozaki(const GemmOzArgs& a, const void* Xs, const void* Y
   if (a.n_items <= 0) return cudaSuccess;
   if (!gemm_ozaki_supported(a.n, a.K) || a.n_items > (1 << 30)) return cudaErrorInvalidValue;
   if (a.slices * kOzTileN > 512) return cudaErrorInvalidValue;
+  int bits = 0, slices = 0;
+  ozaki_params(a.K, &bits, &slices);
+  if (a.bits != bits || a.slices != slices) return cudaErrorInvalidValue;
   CUtensorMap mA, mB;
   if (!encode_slices(&mA, Xs, a.K, a.n, a.n_items, a.slices, kOzTileM) ||
       !encode_slices(&mB, Ys, a.K, a.n, a.n_items, a.slices, kOzTileN))

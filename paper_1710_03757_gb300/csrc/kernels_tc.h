@@ -37,7 +37,7 @@ struct GemmOzArgs {
   int fixed_parity;       // >= 0 overrides the geometry
   const int* expX;        // [n_items][n] row exponents of X (every |x| < 2^e)
   const int* expY;        // [n_items][n] row exponents of Yt
-  int slices;             // slice planes per operand (ozaki_params)
+  int slices, bits;       // slice planes per operand and bits per slice (ozaki_params)
   uint32_t* err;          // set to 1 when a bounded wait expired
 };
 // Slice width b (bits) and slice count s for inner dimension K.

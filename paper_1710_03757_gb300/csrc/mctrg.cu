@@ -645,7 +645,7 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
             GemmOzArgs ga{};
             ga.M = Mb.as<double>(); ga.D = a.D; ga.n = a.n; ga.K = Kd; ga.c0 = i0; ga.n_items = Si;
             ga.Nnew = a.N; ga.L = L; ga.level_new = k; ga.fixed_parity = -1; ga.expX = eX; ga.expY = eY;
-            ga.slices = oz_slices; ga.err = tcErr.as<uint32_t>();
+            ga.slices = oz_slices; ga.bits = oz_bits; ga.err = tcErr.as<uint32_t>();
             CK(timed(MCTRG_K_GEMM, Si, Si * 2.0 * a.n * a.n * Kd,
                      Si * (2.0 * 2.0 * oz_slices * a.n * Kd + 8.0 * a.n * a.n), [&] {
               return launch_gemm_ozaki(ga, tcXh.p, tcYh.p, st); }));
