@@ -233,18 +233,26 @@ struct BdDispatch<NQ + 1, NQ> {
 template <int NQ>
 __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_smem) {
   extern __shared__ double sm[];
-  const int n = a.n;
+  int n = a.n;
   const int mat = blockIdx.x;
   constexpr int NW = kBdThreads / 32;
-  double* A = use_smem ? sm : a.W + (size_t)mat * n * n;
+  const double* Mm;
+  double* Wm;
+  double* bd;
+  if (a.items) {                     // ragged: this matrix's size and buffers
+    const SvdItem& t = a.items[mat];
+    n = t.n; Mm = t.M; Wm = t.W; bd = t.bd;
+    use_smem = ((size_t)n * n + (size_t)(3 + NW) * n + 32) * sizeof(double) <= 200 * 1024;
+  } else {
+    Mm = a.M + (size_t)mat * n * n; Wm = a.W + (size_t)mat * n * n; bd = a.bd + (size_t)mat * 3 * n;
+  }
+  double* A = use_smem ? sm : Wm;
   double* base = use_smem ? sm + (size_t)n * n : sm;
   double* vcol = base;               // [n] column k (then v), below and on the diagonal
   double* wv = vcol + n;             // [n] w
   double* uv = wv + n;               // [n] u
   double* wpart = uv + n;            // [NW][n] per-warp partial column dots
   double* red = wpart + (size_t)NW * n;   // [32]
-  double* bd = a.bd + (size_t)mat * 3 * n;
-  const double* Mm = a.M + (size_t)mat * n * n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ double s_xn2;
   for (int e = tid; e < n * n; e += kBdThreads) A[e] = Mm[e];
@@ -333,7 +341,6 @@ __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_sme
   }
   if (use_smem) {
     __syncthreads();
-    double* Wm = a.W + (size_t)mat * n * n;
     for (int e = tid; e < n * n; e += kBdThreads) Wm[e] = A[e];
   }
 }
@@ -432,15 +439,23 @@ __device__ __forceinline__ double pow2i(int d) {
 // count(lo) <= j < count(hi), so the result is within the final width of the
 // count's crossing, whatever the interpolation does.
 __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int n, int n_pad, double* sig,
-                                                            int* perm, int* nnz, double* lns1, double zero_rel) {
+                                                            int* perm, int* nnz, double* lns1, double zero_rel,
+                                                            const SvdItem* items) {
   extern __shared__ double sm[];
+  int mat = blockIdx.x;
+  if (items) {                       // ragged: this matrix's size and buffers
+    const SvdItem& t = items[mat];
+    bd = t.bd; n = t.n; n_pad = t.n_pad; sig = t.sig; perm = t.perm; nnz = t.nnz; lns1 = t.lns1;
+    zero_rel = t.zero_rel;
+    mat = 0;
+  }
   double* oo = sm;                                   // [2n]
   int* cnt = (int*)(oo + 2 * n);                     // [kBisThreads] FP32 grid counts
   float* oof = (float*)(cnt + kBisThreads);          // [2n] oo in FP32
   __shared__ double red[32];
   __shared__ double s_f0;
   __shared__ int s_zlo, s_nnz, s_e0;
-  const int mat = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const double* d = bd + (size_t)mat * 3 * n;
   const double* e = d + n;
   double* sg = sig + (size_t)mat * n_pad;
@@ -577,19 +592,29 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
 //    previous iterate is folded into the next right-hand side.
 __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a, int ls) {
   const int lane = threadIdx.x;
-  const int n = a.n, m = 2 * n;
-  double* scr = a.scratch + (size_t)blockIdx.x * 4 * m * ls;
+  double* scr = a.scratch + (size_t)blockIdx.x * 4 * (2 * a.n) * ls;   // a slot for the largest n
 #define DG(i) scr[((size_t)0 * m + (i)) * ls + lane]
 #define DU(i) scr[((size_t)1 * m + (i)) * ls + lane]
 #define DU2(i) scr[((size_t)2 * m + (i)) * ls + lane]
 #define XB(i) scr[((size_t)3 * m + (i)) * ls + lane]
 #define XL(l, i) scr[((size_t)3 * m + (i)) * ls + (l)]
   for (int s = blockIdx.x; s < a.S; s += gridDim.x) {
-    const int nk = a.nk[s];
-    const int* kept = a.kept + (size_t)s * 32;
-    const double* sg = a.sig + (size_t)s * a.n_pad;
-    const double* bd = a.bd + (size_t)s * 3 * n;
-    double* vout = a.vrows + (size_t)s * 32 * n;
+    int n = a.n, nk;
+    const int* kept;
+    const double* sg;
+    const double* bd;
+    double* vout;
+    if (a.items) {                   // ragged: this matrix's size and buffers
+      const SvdItem& t = a.items[s];
+      n = t.n; nk = t.nk[0]; kept = t.kept; sg = t.sig; bd = t.bd; vout = t.vrows;
+    } else {
+      nk = a.nk[s];
+      kept = a.kept + (size_t)s * 32;
+      sg = a.sig + (size_t)s * a.n_pad;
+      bd = a.bd + (size_t)s * 3 * n;
+      vout = a.vrows + (size_t)s * 32 * n;
+    }
+    const int m = 2 * n;
     // |T| (max |o_k|): T and s are scaled by 1/|T|, the pivot floor is eps
     double tn = 0.0;
     for (int i = lane; i < n; i += 32) tn = fmax(tn, fmax(fabs(bd[i]), fabs(bd[n + i])));
@@ -752,15 +777,30 @@ __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a, int ls) {
 constexpr int kBtGroup = 16;
 __global__ void __launch_bounds__(128) k_bd_backtr(BdVecArgs a) {
   extern __shared__ double V[];                      // [kBtGroup][n]
-  const int n = a.n, s = blockIdx.x, g0 = blockIdx.y * kBtGroup;
+  const int s = blockIdx.x, g0 = blockIdx.y * kBtGroup;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nk = min(a.nk[s] - g0, kBtGroup);        // vectors of this group
+  int n = a.n, nk_all;
+  double* vrow;
+  const double* R;
+  const double* tauR;
+  const int* kept;
+  const double* sg;
+  if (a.items) {                     // ragged: this matrix's size and buffers
+    const SvdItem& t = a.items[s];
+    n = t.n; nk_all = t.nk[0]; vrow = t.vrows + (size_t)g0 * n; R = t.W; tauR = t.bd + 2 * n;
+    kept = t.kept + g0; sg = t.sig;
+  } else {
+    nk_all = a.nk[s];
+    vrow = a.vrows + ((size_t)s * 32 + g0) * n;
+    R = a.R + (size_t)s * n * n;
+    tauR = a.bd + (size_t)s * 3 * n + 2 * n;
+    kept = a.kept + (size_t)s * 32 + g0;
+    sg = a.sig + (size_t)s * a.n_pad;
+  }
+  const int nk = min(nk_all - g0, kBtGroup);         // vectors of this group
   if (nk <= 0) return;
-  double* vrow = a.vrows + ((size_t)s * 32 + g0) * n;
   for (int e = threadIdx.x; e < nk * n; e += blockDim.x) V[e] = vrow[e];
   __syncthreads();
-  const double* R = a.R + (size_t)s * n * n;
-  const double* tauR = a.bd + (size_t)s * 3 * n + 2 * n;
   const int a0 = warp * 4;
   if (a0 < nk) {
     double* V0 = V + (size_t)a0 * n;
@@ -793,8 +833,6 @@ __global__ void __launch_bounds__(128) k_bd_backtr(BdVecArgs a) {
     }
   }
   __syncthreads();
-  const int* kept = a.kept + (size_t)s * 32 + g0;
-  const double* sg = a.sig + (size_t)s * a.n_pad;
   for (int e = threadIdx.x; e < nk * n; e += blockDim.x) vrow[e] = a.unit_rows ? V[e] : sg[kept[e / n]] * V[e];
 }
 
@@ -813,6 +851,38 @@ static cudaError_t launch_bidiag_nq(const BidiagArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   k_bidiag<NQ><<<a.S, kBdThreads, smem, st>>>(a, use_smem);
   return cudaGetLastError();
+}
+
+// Dynamic shared memory of a launch over matrices of side n (the working copy
+// in shared memory when it fits, else the per-step vectors with enough
+// memory requested that one CTA runs per SM and the matrices stay in L2).
+size_t bidiag_smem_bytes(int n) {
+  const size_t rows = (size_t)n * n * sizeof(double);
+  const size_t aux = ((size_t)(3 + kBdThreads / 32) * n + 32) * sizeof(double);
+  return rows + aux <= 200 * 1024 ? rows + aux : std::max<size_t>(aux, 120 * 1024);
+}
+
+template <int NQ>
+static cudaError_t launch_bidiag_items_nq(const SvdItem* items, int S, size_t smem, cudaStream_t st) {
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t e = raise_smem_limit(k_bidiag<NQ>, 200 * 1024 + 1024, attr);
+  if (e != cudaSuccess) return e;
+  BidiagArgs a{};
+  a.S = S; a.items = items;
+  k_bidiag<NQ><<<S, kBdThreads, smem, st>>>(a, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bidiag_items(const SvdItem* items, int S, int n_max, size_t smem, cudaStream_t st) {
+  if (S <= 0) return cudaSuccess;
+  if (smem > 200 * 1024 + 1024) return cudaErrorInvalidValue;
+  if (n_max <= 64) return launch_bidiag_items_nq<2>(items, S, smem, st);
+  if (n_max <= 128) return launch_bidiag_items_nq<4>(items, S, smem, st);
+  if (n_max <= 256) return launch_bidiag_items_nq<8>(items, S, smem, st);
+  if (n_max <= 512) return launch_bidiag_items_nq<16>(items, S, smem, st);
+  if (n_max <= 768) return launch_bidiag_items_nq<24>(items, S, smem, st);
+  if (n_max <= 1024) return launch_bidiag_items_nq<32>(items, S, smem, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_bidiag(const BidiagArgs& a, cudaStream_t st) {
@@ -834,7 +904,18 @@ cudaError_t launch_bd_bisect(const double* bd, int n, int n_pad, int S, double* 
   static std::atomic<uint64_t> attr{0};
   cudaError_t e = raise_smem_limit(k_bd_bisect, 200 * 1024, attr);
   if (e != cudaSuccess) return e;
-  k_bd_bisect<<<S, kBisThreads, smem, st>>>(bd, n, n_pad, sig, perm, nnz, lns1, zero_rel);
+  k_bd_bisect<<<S, kBisThreads, smem, st>>>(bd, n, n_pad, sig, perm, nnz, lns1, zero_rel, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bd_bisect_items(const SvdItem* items, int S, int n_max, cudaStream_t st) {
+  if (S <= 0) return cudaSuccess;
+  const size_t smem = (size_t)2 * n_max * (sizeof(double) + sizeof(float)) + kBisThreads * sizeof(int);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t e = raise_smem_limit(k_bd_bisect, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
+  k_bd_bisect<<<S, kBisThreads, smem, st>>>(nullptr, 0, 0, nullptr, nullptr, nullptr, nullptr, 0.0, items);
   return cudaGetLastError();
 }
 
@@ -851,6 +932,8 @@ static int invit_slots(int n, int S) {
 // vectors are kept, 32 otherwise).
 size_t bd_vectors_scratch_doubles(int n, int S) { return (size_t)invit_slots(n, S) * 4 * 2 * n * 32; }
 
+// Ragged: a.items holds a.S matrices, a.n the largest side, a.kmax the largest
+// kept count, a.scratch bd_vectors_scratch_doubles(a.n, a.S) doubles.
 cudaError_t launch_bd_vectors(const BdVecArgs& a, cudaStream_t st) {
   if (a.S <= 0) return cudaSuccess;
   const size_t smem = (size_t)kBtGroup * a.n * sizeof(double);

@@ -5,6 +5,23 @@
 
 namespace mctrg {
 
+// One matrix of a ragged launch: matrices of different sizes (and owners) in
+// one launch of the bidiagonalization route, each with its own buffers.
+struct SvdItem {
+  const double* M;    // n x n input
+  double* W;          // n x n working copy; right reflectors on return
+  double* bd;         // 3n: d, e, tauR
+  double* sig;        // n_pad singular values, descending
+  int* perm;          // n_pad
+  int* nnz;           // 1
+  double* lns1;       // 1 (may be null)
+  const int* kept;    // 32 kept ranks (ascending)
+  const int* nk;      // 1
+  double* vrows;      // 32 x n: s_r v_r of the kept ranks
+  double zero_rel;    // zero threshold (<= 0: n 2^-52)
+  int n, n_pad;
+};
+
 // 1. Householder bidiagonalization  Q_L^T M Q_R = B  (upper bidiagonal) of S
 //    row-major n x n matrices.  bd[s] = [d (n) | e (n, e[n-1] = 0) | tauR (n)];
 //    the right reflector of step k, u_k = (1, R[k][k+2], ..., R[k][n-1]) on
@@ -14,8 +31,13 @@ struct BidiagArgs {
   double* W;         // [S][n][n] (any row stride >= n is not supported: n x n)
   double* bd;        // [S][3n]
   int n, S;
+  const SvdItem* items = nullptr;   // ragged: S matrices described here (n = the largest)
 };
 cudaError_t launch_bidiag(const BidiagArgs& a, cudaStream_t st);
+// The same over a ragged set of S matrices (device table; n_max the largest
+// side; smem the largest bidiag_smem_bytes of their sides).
+size_t bidiag_smem_bytes(int n);
+cudaError_t launch_bidiag_items(const SvdItem* items, int S, int n_max, size_t smem, cudaStream_t st);
 
 // 2. All singular values of each B by bisection on Sturm counts of the
 //    Golub-Kahan tridiagonal; written descending into sig[S][n_pad] with
@@ -24,6 +46,8 @@ cudaError_t launch_bidiag(const BidiagArgs& a, cudaStream_t st);
 //    written as 0.
 cudaError_t launch_bd_bisect(const double* bd, int n, int n_pad, int S, double* sig, int* perm, int* nnz,
                              double* lns1, double zero_rel, cudaStream_t st);
+// The same over a ragged set of matrices (n_max = the largest n; device table).
+cudaError_t launch_bd_bisect_items(const SvdItem* items, int S, int n_max, cudaStream_t st);
 
 // 3. Right singular vectors of the kept indices: kept[s][0..nk[s]-1] are
 //    ranks (ascending, so singular values descending).  vrows[s][a][0..n-1]
@@ -42,6 +66,7 @@ struct BdVecArgs {
   int n, n_pad, S;
   int unit_rows;        // 1: write v_r itself instead of s_r v_r
   int kmax;             // largest nk of the batch (<= 32)
+  const SvdItem* items = nullptr;   // ragged: S matrices described here (n = the largest)
 };
 cudaError_t launch_bd_vectors(const BdVecArgs& a, cudaStream_t st);
 size_t bd_vectors_scratch_doubles(int n, int S);
