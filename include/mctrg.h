@@ -113,6 +113,9 @@ typedef struct {
                                  those levels.  A kept and a dropped value closer
                                  than 1e-8 s_1 set MCTRG_FLAG_SPLIT_CLUSTER in every
                                  trajectory.  Negative: EINVAL */
+    const char* autotune_cache; /* mctrg_batch_run: file of the launch geometry chosen
+                                 per matrix shape (read, and written when new shapes
+                                 were timed); NULL = choose every run, keep nothing */
 } mctrg_options;
 
 /* Route of the per-trajectory SVDs (Sec. II, Eq. exactSVD), both FP64 with
@@ -235,6 +238,38 @@ typedef struct {
  * Errors: EINVAL (bad class), ESTATE (profiling off). */
 int mctrg_kernel_stats(mctrg_ctx_t ctx, int kernel, mctrg_kernel_stat* out);
 int mctrg_reset_kernel_stats(mctrg_ctx_t ctx);
+
+/* ---- batching: uneven jobs in one run ----------------------------------- *
+ * A job of a batch: lattice (Sec. IV, the site tensor of mctrg_init_lattice),
+ * bond dimension, n_samples trajectories with counters first_traj ..
+ * first_traj + n_samples - 1 under seed. */
+typedef struct {
+    double beta, h;
+    int L, chi;
+    int64_t n_samples;
+    uint64_t seed;
+    uint64_t first_traj;
+} mctrg_job;
+
+/* Run n_jobs >= 1 jobs of uneven L and chi together on opt->device and
+ * opt->cuda_stream (precision MCTRG_FP64 or MCTRG_FP64TC; the other options
+ * as for mctrg_create).  The jobs' levels advance together in sub-batches:
+ * per job the geometry-dependent kernels (plaquette operands, contraction,
+ * choice of the kept indices, halves), and one launch per stage of the
+ * bidiagonalization-route SVD (Householder reduction, bisection, kept
+ * vectors) over the matrices of every job, of whatever size.  The number of
+ * matrices per SVD launch for each matrix shape and the sampler's CTA count
+ * are launch geometry with identical arithmetic, chosen by timing
+ * candidates on the device and kept in opt->autotune_cache.  Job j's
+ * results are those of mctrg_run with the same lattice, seed and counters,
+ * bit for bit.  Outputs: est[j] (host, required); lnabsZ, sign, flags
+ * (nullable, host or device) receive the jobs' per-trajectory results one
+ * after the other (job 0's n_samples first).  The paper has no counterpart
+ * (it runs one lattice at a time).  Blocks until done.  Errors: EINVAL,
+ * ENOMEM (the jobs' own buffers and one item of the largest shape do not
+ * fit), ECUDA; a job's estimate carries EDOMAIN or ENOCONV in its status. */
+int mctrg_batch_run(const mctrg_options* opt, const mctrg_job* jobs, int n_jobs, mctrg_estimate* est,
+                    double* lnabsZ, int8_t* sign, uint8_t* flags);
 
 /* ---- the batched SVD on its own ------------------------------------------ *
  * Singular values, and optionally right singular vectors, of `batch` row-major

@@ -24,7 +24,7 @@ EXPORTS = [
     "mctrg_server_destroy", "mctrg_plan_level", "mctrg_philox_uniform", "mctrg_kernel_stats",
     "mctrg_reset_kernel_stats", "mctrg_svd_batched", "mctrg_svd_batched_noalloc",
     "mctrg_svd_bidiag_batched", "mctrg_measure_fp64_peak", "mctrg_contract_batched",
-    "mctrg_server_footprint", "mctrg_server_memory",
+    "mctrg_server_footprint", "mctrg_server_memory", "mctrg_batch_run",
 ]
 K_FORM_XY, K_GEMM, K_JACOBI, K_SAMPLE, K_TRACE, K_OTHER, K_BIDIAG, K_BISECT, K_VECTORS, K_COUNT = range(10)
 KERNEL_NAMES = ["form_xy", "gemm", "jacobi", "sample_split", "trace", "other", "bidiag", "bisect", "vectors"]
@@ -40,7 +40,13 @@ class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("max_sweeps", ctypes.c_int),
                 ("max_chunk", ctypes.c_int), ("profile", ctypes.c_int), ("svd", ctypes.c_int),
-                ("zero_tol_scale", ctypes.c_double), ("deterministic_levels", ctypes.c_int)]
+                ("zero_tol_scale", ctypes.c_double), ("deterministic_levels", ctypes.c_int),
+                ("autotune_cache", ctypes.c_char_p)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("h", ctypes.c_double), ("L", ctypes.c_int), ("chi", ctypes.c_int),
+                ("n_samples", ctypes.c_int64), ("seed", ctypes.c_uint64), ("first_traj", ctypes.c_uint64)]
 
 
 class Estimate(ctypes.Structure):
@@ -86,6 +92,8 @@ def lib():
                                           ctypes.POINTER(c_double)]),
             "mctrg_server_destroy": (None, [vp]),
             "mctrg_server_footprint": (c_int, [vp, c_int, c_int, i64, ctypes.POINTER(ctypes.c_size_t)]),
+            "mctrg_batch_run": (c_int, [ctypes.POINTER(Options), ctypes.POINTER(Job), c_int, ctypes.POINTER(Estimate),
+                                        vp, vp, vp]),
             "mctrg_server_memory": (c_int, [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
             "mctrg_plan_level": (c_int, [c_int, c_int, vp, vp]),
             "mctrg_philox_uniform": (c_double, [u64, u32, u32, u32, u32]),
@@ -142,9 +150,11 @@ def mctrg_options_default():
 
 
 def make_options(device=0, stream=None, precision=MCTRG_FP64, hbm_budget_bytes=0, max_sweeps=0,
-                 max_chunk=0, profile=0, svd=SVD_AUTO, zero_tol_scale=0.0, deterministic_levels=0):
+                 max_chunk=0, profile=0, svd=SVD_AUTO, zero_tol_scale=0.0, deterministic_levels=0,
+                 autotune_cache=None):
     o = mctrg_options_default()
     o.deterministic_levels = int(deterministic_levels)
+    o.autotune_cache = autotune_cache.encode() if autotune_cache else None
     o.device, o.precision, o.profile, o.svd = int(device), int(precision), int(profile), int(svd)
     o.zero_tol_scale = float(zero_tol_scale)
     o.cuda_stream = stream
@@ -227,6 +237,17 @@ def mctrg_svd_bidiag_batched(M, sigma, vt=None, stream=None):
     batch, n = int(M.shape[0]), int(M.shape[-1])
     nv = 0 if vt is None else int(vt.shape[1])
     return lib().mctrg_svd_bidiag_batched(_ptr(M), n, batch, _ptr(sigma), nv, _ptr(vt), stream)
+
+
+def mctrg_batch_run(jobs, opts=None, lnabsZ=None, sign=None, flags=None):
+    """jobs: sequence of (beta, h, L, chi, n_samples, seed, first_traj).
+    Returns (status, [Estimate per job])."""
+    arr = (Job * len(jobs))(*[Job(float(b), float(h), int(L), int(c), int(n), int(s), int(f))
+                               for b, h, L, c, n, s, f in jobs])
+    ests = (Estimate * len(jobs))()
+    opts = opts or mctrg_options_default()
+    st = lib().mctrg_batch_run(ctypes.byref(opts), arr, len(jobs), ests, _ptr(lnabsZ), _ptr(sign), _ptr(flags))
+    return st, list(ests)
 
 
 def mctrg_contract_batched(X, Yt, M, precision=MCTRG_FP64, stream=None):
