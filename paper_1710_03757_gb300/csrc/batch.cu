@@ -369,6 +369,8 @@ struct BatchRunner {
     }
     if (!items.empty()) {
       // the ragged SVD launches over every bidiagonalization segment
+      // growing a buffer frees the old one: let the launches that read it finish first
+      if (sizeof(SvdItem) * items.size() > table.bytes) BCK(cudaStreamSynchronize(st));
       BCK(table.ensure(sizeof(SvdItem) * items.size()));
       BCK(cudaMemcpyAsync(table.p, items.data(), sizeof(SvdItem) * items.size(), cudaMemcpyHostToDevice, st));
       const int S = (int)items.size();
@@ -381,6 +383,7 @@ struct BatchRunner {
           BCK(launch_sample_split(sample_args(r, segs[s], ptr[s], 1), st, tuned(a.n, a.kc).sample_grid));
           ++launches;
         }
+      if (sizeof(double) * bd_vectors_scratch_doubles(n_max, S) > vec_scr.bytes) BCK(cudaStreamSynchronize(st));
       BCK(vec_scr.ensure(sizeof(double) * bd_vectors_scratch_doubles(n_max, S)));
       BdVecArgs va{};
       va.n = n_max; va.S = S; va.kmax = kmax; va.items = table.as<SvdItem>(); va.scratch = vec_scr.as<double>();
