@@ -232,36 +232,59 @@ def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_every=10,
                    "chi {8,16,32}, target 1e-6..1e-4)" % literal_every}
 
 
-def measure_uneven(mctrg, n_jobs=32, seed=0xB0A7 + 4):
-    """Jobs of uneven chi and lattice size sharing the device through the server.
-
-    Stand-in of the uneven-batch workload at feasible sizes: chi in {4, 8, 16, 24},
-    L in {8, 16, 32, 64}, beta uniform in [0.3, 0.6], h uniform in [0, 0.1], a fixed
-    number of trajectories each (128-1024), all submitted at once.
-    """
+def _uneven_jobs(n_jobs, seed):
+    """The uneven-batch stand-in: chi in {4, 8, 16, 24}, L in {8, 16, 32, 64} (L <= 32 for
+    chi > 8), beta uniform in [0.3, 0.6], h uniform in [0, 0.1], 64-512 trajectories each."""
     import numpy as np
     rng = np.random.default_rng(seed)
+    jobs = []
+    for _ in range(n_jobs):
+        chi = int(rng.choice([4, 8, 16, 24]))
+        L = int(rng.choice([8, 16, 32, 64] if chi <= 8 else [8, 16, 32]))
+        n = int(rng.integers(64, 513))
+        jobs.append((float(rng.uniform(0.3, 0.6)), float(rng.uniform(0, 0.1)), L, chi, n,
+                     int(rng.integers(1 << 62)), 0))
+    return jobs
+
+
+def measure_uneven(mctrg, n_jobs=24, seed=0xB0A7 + 4):
+    """Jobs of uneven chi and lattice size: (a) through the server (each job on a
+    worker's stream, FP64), (b) as one batch (levels advanced together, the SVD
+    stages in ragged launches over every job's matrices, autotuned launch
+    geometry), FP64, and (c) the batch with the FP64-accurate tensor-core
+    contraction.  The same jobs and counters in every run: each job's ln Z^ must
+    agree (to the rounding of the server's merge of its rounds)."""
+    import numpy as np
+    jobs = _uneven_jobs(n_jobs, seed)
+    traj = sum(j[4] for j in jobs)
+    out = {"jobs": n_jobs, "trajectories": traj,
+           "mix": "chi {4,8,16,24}, L {8..64}, beta U[0.3,0.6], h U[0,0.1], 64-512 trajectories each"}
     srv = mctrg.mctrg_server_create()
     t0 = time.perf_counter()
     ids = []
     try:
-        for _ in range(n_jobs):
-            chi = int(rng.choice([4, 8, 16, 24]))
-            L = int(rng.choice([8, 16, 32, 64] if chi <= 8 else [8, 16, 32]))
-            n = int(rng.integers(128, 1025))
-            st, j = mctrg.mctrg_server_submit(srv, float(rng.uniform(0.3, 0.6)), float(rng.uniform(0, 0.1)),
-                                              L, chi, 1e-12, n, int(rng.integers(1 << 62)))
-            if st == 0:
-                ids.append(j)
-        traj = 0
-        for j in ids:
-            st, est, l = mctrg.mctrg_server_wait(srv, j, 900.0)
-            traj += est.n
+        for b, h, L, chi, n, sd, _ in jobs:
+            st, j = mctrg.mctrg_server_submit(srv, b, h, L, chi, 1e-12, n, sd)
+            ids.append(j)
+        srv_est = [mctrg.mctrg_server_wait(srv, j, 1800.0)[1] for j in ids]
         wall = time.perf_counter() - t0
     finally:
         mctrg.mctrg_server_destroy(srv)
-    return {"jobs": len(ids), "trajectories": traj, "seconds": wall, "trajectories_per_s": traj / wall,
-            "mix": "chi {4,8,16,24}, L {8..64}, beta U[0.3,0.6], h U[0,0.1], 128-1024 trajectories each"}
+    out["server_fp64"] = {"seconds": wall, "trajectories_per_s": traj / wall}
+    import tempfile
+    cache = os.path.join(tempfile.gettempdir(), "mctrg_autotune_cache.txt")
+    for name, prec in (("batch_fp64", mctrg.MCTRG_FP64), ("batch_fp64tc", mctrg.MCTRG_FP64TC)):
+        opts = mctrg.make_options(precision=prec, autotune_cache=cache)
+        mctrg.mctrg_batch_run(jobs[:2], opts)          # tunes the shapes once (kept in the cache)
+        t0 = time.perf_counter()
+        st, ests = mctrg.mctrg_batch_run(jobs, opts)
+        wall = time.perf_counter() - t0
+        dev = max(abs(a.ln_mean_Z - b.ln_mean_Z) / abs(b.ln_mean_Z) for a, b in zip(ests, srv_est)
+                  if np.isfinite(a.ln_mean_Z) and np.isfinite(b.ln_mean_Z))
+        out[name] = {"status": mctrg.mctrg_strerror(st), "seconds": wall, "trajectories_per_s": traj / wall,
+                     "max_rel_lnZ_vs_server": dev}
+    out["trajectories_per_s"] = out["batch_fp64tc"]["trajectories_per_s"]
+    return out
 
 
 def run_reference(args, wl, rank, world):
