@@ -287,6 +287,37 @@ def measure_uneven(mctrg, n_jobs=24, seed=0xB0A7 + 4):
     return out
 
 
+def _time_to_se(est, rate, targets=(1e-1, 1e-2)):
+    """Trajectories and seconds to reach a standard error of ln Z, projected from this run's
+    estimate by the 1/sqrt(N) law (Sec. V, Eq. shrunkDev) at this run's rate."""
+    if not (est.n > 1 and est.se_ln_Z > 0 and math.isfinite(est.se_ln_Z) and rate > 0):
+        return None
+    out = {}
+    for t in targets:
+        n = est.n * (est.se_ln_Z / t) ** 2
+        out["se_%g" % t] = {"trajectories": n, "seconds": n / rate}
+    return out
+
+
+def measure_time_to_se(mctrg, precision=0, L=32, chi=16, beta=0.44, n=2048, target=1e-3):
+    """Time to a stated standard error of ln Z on the 32 x 32 lattice (chi = 16): n
+    trajectories, their SE, the trajectories the target needs by the 1/sqrt(N) law and the
+    time at the measured rate (this lattice's estimator is well behaved: ESS near n)."""
+    ctx = mctrg.mctrg_create(mctrg.make_options(precision=precision))
+    try:
+        assert mctrg.mctrg_init_lattice(ctx, beta, 0.0, L, chi) == 0
+        mctrg.mctrg_run(ctx, 64, 0x5E, 10 ** 6)             # warm
+        t0 = time.perf_counter()
+        st, est = mctrg.mctrg_run(ctx, n, 0x5E, 0)
+        dt = time.perf_counter() - t0
+    finally:
+        mctrg.mctrg_destroy(ctx)
+    need = n * (est.se_ln_Z / target) ** 2
+    return {"lattice": "Ising %dx%d, chi=%d, beta=%g" % (L, L, chi, beta), "trajectories": n,
+            "seconds": dt, "trajectories_per_s": n / dt, "se_ln_Z": est.se_ln_Z, "ess": est.ess,
+            "target_se_ln_Z": target, "trajectories_needed": need, "seconds_needed": need * dt / n}
+
+
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return
@@ -556,7 +587,12 @@ def main():
             "mixed": mixed,
             "gpu_launches": launches, "roofline": roof, "kernels": kernels,
             "estimate": {"ln_mean_Z": merged.ln_mean_Z, "se_ln_Z": merged.se_ln_Z, "n": merged.n,
-                         "ess": merged.ess, "n_flagged": merged.n_flagged},
+                         "ess": merged.ess, "n_flagged": merged.n_flagged,
+                         "note": ("effective sample size %.2f of %d: the estimate is dominated by its largest "
+                                  "trajectories and its SE is not reliable" % (merged.ess, merged.n))
+                         if merged.ess < 0.2 * merged.n else "effective sample size %.1f of %d" % (merged.ess,
+                                                                                                   merged.n)},
+            "time_to_se": _time_to_se(merged, value),
             "clocks": clk.summary()}
     mctrg.mctrg_destroy(ctx)
     if args.serve_seconds > 0:
@@ -564,6 +600,11 @@ def main():
             line["serve"] = measure_serving(mctrg, args.serve_seconds, args.serve_load)
         except Exception as e:
             line["serve"] = {"error": repr(e)[:200]}
+    try:
+        line["time_to_se_32x32"] = {"fp64": measure_time_to_se(mctrg, 0),
+                                    "fp64tc": measure_time_to_se(mctrg, mctrg.MCTRG_FP64TC)}
+    except Exception as e:
+        line["time_to_se_32x32"] = {"error": repr(e)[:200]}
     if not args.no_uneven:
         try:
             line["uneven_batch"] = measure_uneven(mctrg)
