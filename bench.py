@@ -264,13 +264,14 @@ def measure_uneven(mctrg, n_jobs=24, seed=0xB0A7 + 4):
     ids = []
     try:
         for b, h, L, chi, n, sd, _ in jobs:
-            st, j = mctrg.mctrg_server_submit(srv, b, h, L, chi, 1e-12, n, sd)
+            st, j = mctrg.mctrg_server_submit(srv, b, h, L, chi, 0.0, n, sd)   # fixed-sample job
             ids.append(j)
         srv_est = [mctrg.mctrg_server_wait(srv, j, 1800.0)[1] for j in ids]
         wall = time.perf_counter() - t0
     finally:
         mctrg.mctrg_server_destroy(srv)
-    out["server_fp64"] = {"seconds": wall, "trajectories_per_s": traj / wall}
+    srv_traj = sum(e.n for e in srv_est)
+    out["server_fp64"] = {"seconds": wall, "trajectories": srv_traj, "trajectories_per_s": srv_traj / wall}
     import tempfile
     cache = os.path.join(tempfile.gettempdir(), "mctrg_autotune_cache.txt")
     for name, prec in (("batch_fp64", mctrg.MCTRG_FP64), ("batch_fp64tc", mctrg.MCTRG_FP64TC)):
@@ -279,10 +280,11 @@ def measure_uneven(mctrg, n_jobs=24, seed=0xB0A7 + 4):
         t0 = time.perf_counter()
         st, ests = mctrg.mctrg_batch_run(jobs, opts)
         wall = time.perf_counter() - t0
-        dev = max(abs(a.ln_mean_Z - b.ln_mean_Z) / abs(b.ln_mean_Z) for a, b in zip(ests, srv_est)
-                  if np.isfinite(a.ln_mean_Z) and np.isfinite(b.ln_mean_Z))
+        same = [(a, b) for a, b in zip(ests, srv_est) if a.n == b.n]   # jobs that ran the same trajectories
+        dev = max([abs(a.ln_mean_Z - b.ln_mean_Z) / abs(b.ln_mean_Z) for a, b in same
+                   if np.isfinite(a.ln_mean_Z) and np.isfinite(b.ln_mean_Z)] or [0.0])
         out[name] = {"status": mctrg.mctrg_strerror(st), "seconds": wall, "trajectories_per_s": traj / wall,
-                     "max_rel_lnZ_vs_server": dev}
+                     "max_rel_lnZ_vs_server": dev, "jobs_compared_with_server": len(same)}
     out["trajectories_per_s"] = out["batch_fp64tc"]["trajectories_per_s"]
     return out
 

@@ -386,8 +386,10 @@ const char* mctrg_strerror(int status);
 typedef struct mctrg_server* mctrg_server_t;
 
 int mctrg_server_create(const mctrg_options* opt, mctrg_server_t* out);
-/* Non-blocking.  target_se_lnZ > 0; max_samples >= 1.  Returns EUNREACHABLE
- * at once when even one trajectory of the job cannot fit the server's budget. */
+/* Non-blocking.  target_se_lnZ >= 0 (0: a fixed-sample job that runs exactly
+ * max_samples trajectories, no early stop); max_samples >= 1.  Returns
+ * EUNREACHABLE at once when even one trajectory of the job cannot fit the
+ * server's budget. */
 int mctrg_server_submit(mctrg_server_t srv, double beta, double h, int L, int chi,
                         double target_se_lnZ, int64_t max_samples, uint64_t seed,
                         uint64_t* job_id);

@@ -298,19 +298,59 @@ struct BatchRunner {
   }
 
   // ---- one sub-batch ---------------------------------------------------------
+  // The segments' own kernels run on a pool of streams (forked from and joined
+  // back to the batch's stream around each merged stage), so the small
+  // launches of different jobs overlap on the device as the server's workers'
+  // do; each stream has its own region of the sampler's scratch.
+  static constexpr int kStreams = 8;
+  cudaStream_t pool[kStreams] = {};
+  std::vector<cudaEvent_t> evs;
+  size_t smp_region = 0;          // doubles of sampler scratch per stream
+
+  int make_pool() {
+    for (int i = 0; i < kStreams; ++i)
+      BCK(cudaStreamCreateWithFlags(&pool[i], cudaStreamNonBlocking));
+    evs.resize(kStreams + 1);
+    for (cudaEvent_t& e : evs) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return MCTRG_OK;
+  }
+  void free_pool() {
+    for (cudaStream_t& p : pool) if (p) { cudaStreamDestroy(p); p = nullptr; }
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    evs.clear();
+  }
+  // the pool's streams wait for the batch stream's work so far
+  int fork(int used) {
+    BCK(cudaEventRecord(evs[kStreams], st));
+    for (int i = 0; i < used; ++i) BCK(cudaStreamWaitEvent(pool[i], evs[kStreams], 0));
+    return MCTRG_OK;
+  }
+  // the batch stream waits for the pool's work
+  int join(int used) {
+    for (int i = 0; i < used; ++i) {
+      BCK(cudaEventRecord(evs[i], pool[i]));
+      BCK(cudaStreamWaitEvent(st, evs[i], 0));
+    }
+    return MCTRG_OK;
+  }
+
   int run_segments(const std::vector<Segment>& segs) {
     char* base = (char*)ws.p;
     const int prec = opt.precision;
     const bool oz_mode = prec == MCTRG_FP64TC;
     const bool tc_mode = prec != MCTRG_FP64 && !oz_mode;
+    const int used = (int)std::min<size_t>(segs.size(), kStreams);
     std::vector<SegPtrs> ptr(segs.size());
     std::vector<SvdItem> items;
+    std::vector<int> item_n;          // side of each item (for chunking by shape)
     int n_max = 0, kmax = 0;
     size_t smem = 0;
+    BCK(fork(used) == MCTRG_OK ? cudaSuccess : cudaErrorUnknown);
     for (size_t s = 0; s < segs.size(); ++s) {
       const Segment& g = segs[s];
       JobRun& r = jr[g.j];
       mctrg_ctx* c = r.ctx;
+      cudaStream_t ss = pool[s % kStreams];
       const LevelInfo& a = c->lv[g.k];
       const LevelInfo& p = c->lv[g.k - 1];
       const ItemLayout L = layout(c, g.k, prec);
@@ -320,19 +360,19 @@ struct BatchRunner {
       xa.H = c->Hbuf[r.prev].as<double>(); xa.h_item0 = 0; xa.d = p.D; xa.D = p.kc; xa.c0 = g.i0;
       xa.n_items = g.cnt; xa.Nnew = a.N; xa.Nold = p.N; xa.L = c->L; xa.level_old = g.k - 1;
       xa.fixed_parents = 0; xa.X = q.X; xa.Yt = q.Y;
-      BCK(launch_form_xy(xa, st));
+      BCK(launch_form_xy(xa, ss));
       const int Kd = p.D * p.D;
       const int tc_kind = (prec == MCTRG_TF32 || prec == MCTRG_TF32X3) ? 0 : 1;
       if (oz_mode && gemm_ozaki_supported(a.n, Kd)) {
         int bits, slices;
         ozaki_params(Kd, &bits, &slices);
-        BCK(launch_ozaki_split(q.X, g.cnt * a.n, Kd, q.ozX, q.ezX, st));
-        BCK(launch_ozaki_split(q.Y, g.cnt * a.n, Kd, q.ozY, q.ezY, st));
+        BCK(launch_ozaki_split(q.X, g.cnt * a.n, Kd, q.ozX, q.ezX, ss));
+        BCK(launch_ozaki_split(q.Y, g.cnt * a.n, Kd, q.ozY, q.ezY, ss));
         GemmOzArgs ga{};
         ga.M = q.M; ga.D = a.D; ga.n = a.n; ga.K = Kd; ga.c0 = g.i0; ga.n_items = g.cnt; ga.Nnew = a.N;
         ga.L = c->L; ga.level_new = g.k; ga.fixed_parity = -1; ga.expX = q.ezX; ga.expY = q.ezY;
         ga.slices = slices; ga.bits = bits; ga.err = err.as<uint32_t>();
-        BCK(launch_gemm_ozaki(ga, q.ozX, q.ozY, st));
+        BCK(launch_gemm_ozaki(ga, q.ozX, q.ozY, ss));
         launches += 3;
       } else if (tc_mode && gemm_tc_supported(a.n, Kd, tc_kind)) {
         return MCTRG_EINVAL;   // the TF32/BF16 modes run through mctrg_run, not batches
@@ -340,7 +380,7 @@ struct BatchRunner {
         GemmArgs gm{};
         gm.X = q.X; gm.Yt = q.Y; gm.M = q.M; gm.D = a.D; gm.K = Kd; gm.c0 = g.i0; gm.n_items = g.cnt;
         gm.Nnew = a.N; gm.L = c->L; gm.level_new = g.k; gm.fixed_parity = -1;
-        BCK(launch_gemm_f64(gm, st));
+        BCK(launch_gemm_f64(gm, ss));
         ++launches;
       }
       launches += 1;
@@ -352,6 +392,7 @@ struct BatchRunner {
           t.lns1 = c->ilns1.as<double>() + g.i0 + i; t.kept = q.kept + (size_t)i * 32; t.nk = q.nk + i;
           t.vrows = q.vrows + (size_t)i * 32 * a.n; t.zero_rel = zero_fp64(a.n); t.n = a.n; t.n_pad = a.n_pad;
           items.push_back(t);
+          item_n.push_back(a.n);
         }
         n_max = std::max(n_max, a.n);
         kmax = std::max(kmax, a.kc);
@@ -362,45 +403,61 @@ struct BatchRunner {
         ja.M = q.M; ja.W = q.W; ja.sig = q.sig; ja.perm = q.perm; ja.lns1 = c->ilns1.as<double>() + g.i0;
         ja.nnz = q.nnz; ja.mflags = c->iflags.as<uint32_t>() + g.i0; ja.n = a.n; ja.n_pad = a.n_pad;
         ja.S = (int)g.cnt; ja.max_sweeps = c->opt.max_sweeps; ja.zero_rel = zero_fp64(a.n);
-        BCK(launch_jacobi(ja, st));
-        BCK(launch_sample_split(sample_args(r, g, q, 0), st, tuned(a.n, a.kc).sample_grid));
+        BCK(launch_jacobi(ja, ss));
+        BCK(launch_sample_split(sample_args(r, g, q, 0, s), ss, tuned(a.n, a.kc).sample_grid));
         launches += 2;
       }
     }
+    BCK(join(used) == MCTRG_OK ? cudaSuccess : cudaErrorUnknown);
     if (!items.empty()) {
-      // the ragged SVD launches over every bidiagonalization segment
-      // growing a buffer frees the old one: let the launches that read it finish first
+      // the ragged SVD launches over every bidiagonalization segment, in chunks of
+      // the tuned size of the largest shape present
       if (sizeof(SvdItem) * items.size() > table.bytes) BCK(cudaStreamSynchronize(st));
       BCK(table.ensure(sizeof(SvdItem) * items.size()));
       BCK(cudaMemcpyAsync(table.p, items.data(), sizeof(SvdItem) * items.size(), cudaMemcpyHostToDevice, st));
       const int S = (int)items.size();
-      BCK(launch_bidiag_items(table.as<SvdItem>(), S, n_max, smem, st));
-      BCK(launch_bd_bisect_items(table.as<SvdItem>(), S, n_max, st));
+      const int chunk = std::max(1, tuned(n_max, kmax).svd_items);
+      for (int i0 = 0; i0 < S; i0 += chunk) {
+        const int cnt = std::min(chunk, S - i0);
+        BCK(launch_bidiag_items(table.as<SvdItem>() + i0, cnt, n_max, smem, st));
+        BCK(launch_bd_bisect_items(table.as<SvdItem>() + i0, cnt, n_max, st));
+        launches += 2;
+      }
+      BCK(fork(used) == MCTRG_OK ? cudaSuccess : cudaErrorUnknown);
       for (size_t s = 0; s < segs.size(); ++s)
         if (segs[s].bidiag) {
           JobRun& r = jr[segs[s].j];
           const LevelInfo& a = r.ctx->lv[segs[s].k];
-          BCK(launch_sample_split(sample_args(r, segs[s], ptr[s], 1), st, tuned(a.n, a.kc).sample_grid));
+          BCK(launch_sample_split(sample_args(r, segs[s], ptr[s], 1, s), pool[s % kStreams],
+                                  tuned(a.n, a.kc).sample_grid));
           ++launches;
         }
-      if (sizeof(double) * bd_vectors_scratch_doubles(n_max, S) > vec_scr.bytes) BCK(cudaStreamSynchronize(st));
-      BCK(vec_scr.ensure(sizeof(double) * bd_vectors_scratch_doubles(n_max, S)));
-      BdVecArgs va{};
-      va.n = n_max; va.S = S; va.kmax = kmax; va.items = table.as<SvdItem>(); va.scratch = vec_scr.as<double>();
-      BCK(launch_bd_vectors(va, st));
+      BCK(join(used) == MCTRG_OK ? cudaSuccess : cudaErrorUnknown);
+      const size_t vneed = sizeof(double) * bd_vectors_scratch_doubles(n_max, std::min(S, chunk));
+      if (vneed > vec_scr.bytes) BCK(cudaStreamSynchronize(st));
+      BCK(vec_scr.ensure(vneed));
+      for (int i0 = 0; i0 < S; i0 += chunk) {
+        BdVecArgs va{};
+        va.n = n_max; va.S = std::min(chunk, S - i0); va.kmax = kmax; va.items = table.as<SvdItem>() + i0;
+        va.scratch = vec_scr.as<double>();
+        BCK(launch_bd_vectors(va, st));
+        launches += 2;
+      }
+      BCK(fork(used) == MCTRG_OK ? cudaSuccess : cudaErrorUnknown);
       for (size_t s = 0; s < segs.size(); ++s)
         if (segs[s].bidiag) {
           JobRun& r = jr[segs[s].j];
           const LevelInfo& a = r.ctx->lv[segs[s].k];
-          BCK(launch_sample_split(sample_args(r, segs[s], ptr[s], 2), st, tuned(a.n, a.kc).sample_grid));
+          BCK(launch_sample_split(sample_args(r, segs[s], ptr[s], 2, s), pool[s % kStreams],
+                                  tuned(a.n, a.kc).sample_grid));
           ++launches;
         }
-      launches += 4;
+      BCK(join(used) == MCTRG_OK ? cudaSuccess : cudaErrorUnknown);
     }
     return MCTRG_OK;
   }
 
-  SampleArgs sample_args(JobRun& r, const Segment& g, const SegPtrs& q, int mode) {
+  SampleArgs sample_args(JobRun& r, const Segment& g, const SegPtrs& q, int mode, size_t s) {
     mctrg_ctx* c = r.ctx;
     const LevelInfo& a = c->lv[g.k];
     SampleArgs sa{};
@@ -408,7 +465,7 @@ struct BatchRunner {
     sa.n = a.n; sa.n_pad = a.n_pad; sa.chi = c->chi; sa.kc = a.kc; sa.stochastic = 1; sa.shared_svd = 0;
     sa.item0 = g.i0; sa.n_items = g.cnt; sa.N = a.N; sa.L = c->L; sa.level = g.k; sa.seed = r.job.seed;
     sa.traj0 = r.job.first_traj; sa.H = c->Hbuf[r.cur].as<double>(); sa.h_item0 = 0;
-    sa.iflags = c->iflags.as<uint32_t>(); sa.scratch = smp_scr.as<double>();
+    sa.iflags = c->iflags.as<uint32_t>(); sa.scratch = smp_scr.as<double>() + (s % kStreams) * smp_region;
     sa.mode = mode;
     if (mode == 0) { sa.W = q.W; }
     else { sa.W = nullptr; sa.kept = q.kept; sa.sigt = q.sigt; sa.nk = q.nk; sa.vrows = q.vrows; }
@@ -419,7 +476,8 @@ struct BatchRunner {
   // For one shape (n, kc) of the bidiagonalization route: matrices per SVD
   // launch among 1, 2, 4, 8 and 16 per SM, timed on random matrices of that
   // shape (each candidate's launches over the same number of matrices); the
-  // smallest count within 3% of the best rate is kept.  The sampler's CTA
+  // count with the best rate is kept (it sets the chunks of the merged SVD
+  // launches).  The sampler's CTA
   // count is timed the same way on the choice pass.  Every candidate computes
   // the same numbers; only the launch geometry differs.
   int tune_shape(int n, int kc) {
@@ -497,7 +555,7 @@ struct BatchRunner {
     for (double r : rate) best = std::max(best, r);
     int pick = 1;
     for (int ci = 0; ci < 5; ++ci)
-      if (rate[ci] > 0.0 && rate[ci] >= 0.97 * best) { pick = cands[ci]; break; }
+      if (rate[ci] > 0.0 && rate[ci] >= best) pick = cands[ci];
     tune[TuneKey{n, kc}] = TuneVal{pick * sms, 8 * sms};
     tune_dirty = true;
     return MCTRG_OK;
@@ -570,8 +628,10 @@ extern "C" int mctrg_batch_run(const mctrg_options* opt, const mctrg_job* jobs, 
           for (int k = r.ctx->s0 + 1; k < r.ctx->nlev; ++k)
             scr = std::max(scr, sample_scratch_doubles(r.ctx->lv[k].n, r.ctx->chi,
                                                        R.tuned(r.ctx->lv[k].n, r.ctx->lv[k].kc).sample_grid));
-      if (status == MCTRG_OK && R.smp_scr.ensure(sizeof(double) * std::max<size_t>(scr, 1)) != cudaSuccess)
+      R.smp_region = std::max<size_t>(scr, 1);
+      if (status == MCTRG_OK && R.smp_scr.ensure(sizeof(double) * R.smp_region * BatchRunner::kStreams) != cudaSuccess)
         status = MCTRG_ENOMEM;
+      if (status == MCTRG_OK) status = R.make_pool();
       if (status == MCTRG_OK && cudaMemsetAsync(R.err.p, 0, sizeof(uint32_t), R.st) != cudaSuccess)
         status = MCTRG_ECUDA;
       // sub-batches until every job has finished its levels
@@ -587,11 +647,13 @@ extern "C" int mctrg_batch_run(const mctrg_options* opt, const mctrg_job* jobs, 
           const ItemLayout L = layout(c, r.k, R.opt.precision);
           const int Kd = c->lv[r.k - 1].D * c->lv[r.k - 1].D;
           const bool bd = c->use_bidiag(c->lv[r.k].n, Kd);
-          int64_t cap = r.items - r.next;
-          if (bd) cap = std::min<int64_t>(cap, R.tuned(c->lv[r.k].n, c->lv[r.k].kc).svd_items);
-          cap = std::min<int64_t>(cap, 1 << 16);
+          int64_t cap = std::min<int64_t>(r.items - r.next, 1 << 16);
+          // every job still at work gets an equal share of the workspace
+          int active = 0;
+          for (const JobRun& o : R.jr) active += !o.done;
+          const size_t share = std::max<size_t>(R.ws.bytes / std::max(1, active), segment_bytes(L, 1));
           int64_t cnt = cap;
-          while (cnt > 0 && used + segment_bytes(L, cnt) > R.ws.bytes) cnt /= 2;
+          while (cnt > 0 && (used + segment_bytes(L, cnt) > R.ws.bytes || segment_bytes(L, cnt) > share)) cnt /= 2;
           if (cnt <= 0) continue;
           segs.push_back(Segment{j, r.k, r.next, cnt, used, bd});
           used += segment_bytes(L, cnt);
@@ -655,7 +717,8 @@ extern "C" int mctrg_batch_run(const mctrg_options* opt, const mctrg_job* jobs, 
     if (e.status == MCTRG_OK && c->any_noconv(B)) e.status = MCTRG_ENOCONV;
     off += B;
   }
-  for (JobRun& r : R.jr) mctrg_destroy(r.ctx);
   cudaStreamSynchronize(R.st);
+  R.free_pool();
+  for (JobRun& r : R.jr) mctrg_destroy(r.ctx);
   return status;
 }

@@ -119,6 +119,7 @@ struct mctrg_server {
         mctrg_merge_estimates(parts, 2, &total);
       }
       done += R;
+      if (j->target == 0.0) { round = std::min(round * 2, kRoundMax); continue; }   // fixed-sample job
       if (total.status == MCTRG_OK && total.se_ln_Z <= j->target) { reached = true; break; }
       // projection of the standard error to max_samples (1/sqrt(N)); a margin
       // of 2 absorbs the scatter of an early estimate of it
@@ -127,7 +128,7 @@ struct mctrg_server {
         break;
       round = std::min(round * 2, kRoundMax);
     }
-    if (status == MCTRG_OK && !reached) status = MCTRG_EUNREACHABLE;
+    if (status == MCTRG_OK && !reached && j->target > 0.0) status = MCTRG_EUNREACHABLE;
     std::lock_guard<std::mutex> lk(mu);
     j->est = total;
     j->status = status;
@@ -227,7 +228,7 @@ extern "C" int mctrg_server_submit(mctrg_server_t s, double beta, double h, int 
                                    uint64_t* job_id) {
   if (!s || !job_id) return MCTRG_EINVAL;
   if (L < 2 || (L & (L - 1)) || L > 65536 || chi < 1 || chi > 32 || !(beta >= 0) ||
-      !std::isfinite(beta) || !std::isfinite(h) || !(target_se_lnZ > 0) || max_samples < 1 ||
+      !std::isfinite(beta) || !std::isfinite(h) || !(target_se_lnZ >= 0) || max_samples < 1 ||
       (uint64_t)max_samples > (1ull << 32))
     return MCTRG_EINVAL;
   Job* j = new Job();

@@ -172,3 +172,25 @@ def test_literal_configurations_are_refused_fast():
         print("literal jobs refused or projected out of reach in %.1f s" % (time.time() - t))
     finally:
         mctrg.mctrg_server_destroy(srv)
+
+
+def test_fixed_sample_job_runs_exactly_max_samples():
+    # target 0: no early stop; the rounds (256, 512, then the rest) merge to the
+    # estimate of one run over the same counters (to the rounding of the merge)
+    srv = mctrg.mctrg_server_create()
+    try:
+        st, j = mctrg.mctrg_server_submit(srv, 0.44, 0.0, 16, 8, 0.0, 1000, 21)
+        assert st == 0
+        st, est, _ = mctrg.mctrg_server_wait(srv, j, 300.0)
+        assert st == mctrg.MCTRG_OK and est.n == 1000
+    finally:
+        mctrg.mctrg_server_destroy(srv)
+    ctx = mctrg.mctrg_create()
+    try:
+        assert mctrg.mctrg_init_lattice(ctx, 0.44, 0.0, 16, 8) == 0
+        st, ref = mctrg.mctrg_run(ctx, 1000, 21, 0)
+    finally:
+        mctrg.mctrg_destroy(ctx)
+    assert abs(est.ln_mean_Z - ref.ln_mean_Z) <= 1e-13 * abs(ref.ln_mean_Z)
+    assert abs(est.se_ln_Z - ref.se_ln_Z) <= 1e-10 * ref.se_ln_Z
+    assert est.n_negative == ref.n_negative and est.n_flagged == ref.n_flagged
