@@ -80,6 +80,21 @@ def test_chi32_tensor_core_levels():
     assert np.median(np.abs(ln - ln0) / np.abs(ln0)) <= 1e-6
 
 
+def test_chi32_fp64tc_against_oracle():
+    # chi = 32: inner dimension 1024, so the split uses 7-bit slices (8 of
+    # them, 36 exact slice products, eight accumulators filling tensor memory);
+    # per trajectory against the oracle at the FP64 bound
+    L, chi, n, seed = 8, 32, 6, 31
+    st, est, ln, sg = run(mctrg.MCTRG_FP64TC, L=L, chi=chi, n=n, seed=seed, beta=0.3)
+    assert st == 0
+    os_, ol, of = run_many(Problem(ising.site_tensor(0.3, 0.0), L, chi), seed, 0, n, workers=n)
+    ok = of == 0
+    assert ok.sum() >= n - 1
+    np.testing.assert_array_equal(sg[ok], os_[ok])
+    rel = np.abs(ln[ok] - ol[ok]) / np.maximum(1.0, np.abs(ol[ok]))
+    assert rel.max() <= 1e-10, rel.max()
+
+
 # per-trajectory bounds against the oracle (maximum relative ln Z error, and
 # maximum absolute ln Z error per site), measured on GB300 with these seeds:
 # TF32X3 6.8e-8 / 6.3e-8 at 32 x 32 and 64 x 64, within the 1e-6 target;
