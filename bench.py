@@ -276,7 +276,8 @@ def measure_uneven(mctrg, n_jobs=24, seed=0xB0A7 + 4):
     cache = os.path.join(tempfile.gettempdir(), "mctrg_autotune_cache.txt")
     for name, prec in (("batch_fp64", mctrg.MCTRG_FP64), ("batch_fp64tc", mctrg.MCTRG_FP64TC)):
         opts = mctrg.make_options(precision=prec, autotune_cache=cache)
-        mctrg.mctrg_batch_run(jobs[:2], opts)          # tunes the shapes once (kept in the cache)
+        # one trajectory per job first: every shape of the batch is tuned (and cached) before timing
+        mctrg.mctrg_batch_run([(b, h, L, chi, 1, sd, 0) for b, h, L, chi, _, sd, _ in jobs], opts)
         t0 = time.perf_counter()
         st, ests = mctrg.mctrg_batch_run(jobs, opts)
         wall = time.perf_counter() - t0
