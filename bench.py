@@ -157,7 +157,7 @@ def _serve_literal(rng):
             int(rng.choice([8, 16, 32])), float(10 ** rng.uniform(-6, -4)), 1 << 18, int(rng.integers(1 << 62)))
 
 
-def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_every=10, drain_s=120.0, burst_jobs=16):
+def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_every=3, drain_s=120.0, burst_jobs=16):
     """Continuous batching under Poisson arrivals at a stated fraction of capacity.
 
     Job mix (small-lattice stand-in of the serving workload): beta uniform in
@@ -506,7 +506,11 @@ def main():
             gst = mctrg.mctrg_kernel_stats(cm, mctrg.K_GEMM)
             mctrg.mctrg_destroy(cm)
             got = np.concatenate([o[0].cpu().numpy() for o in outs_m])
-            ok = np.isfinite(ref) & np.isfinite(got)
+            # near-tie trajectories (flagged in either run) may keep different indices: left out,
+            # as in the parity tests, and counted
+            fl = np.concatenate([o[2].cpu().numpy() for o in outs]) | np.concatenate([o[2].cpu().numpy()
+                                                                                     for o in outs_m])
+            ok = np.isfinite(ref) & np.isfinite(got) & (fl == 0)
             rel = np.abs(got[ok] - ref[ok]) / np.abs(ref[ok])
             em = mctrg.mctrg_merge_estimates(ests_m)
             # executed tensor-pipe flops of the contraction: passes (TF32X3) or slice
@@ -523,7 +527,8 @@ def main():
                 if rel.size else None,
                 "lnZhat_rel_err": abs(em.ln_mean_Z - e64.ln_mean_Z) / abs(e64.ln_mean_Z)
                 if np.isfinite(em.ln_mean_Z) and np.isfinite(e64.ln_mean_Z) else None,
-                "errors_against": "the FP64 path on the same trajectories (parity-tested against the FP64 oracle)",
+                "errors_against": "the FP64 path on the same trajectories (parity-tested against the FP64 oracle), "
+                                  "unflagged ones: %d of %d" % (int(ok.sum()), len(ok)),
                 "contraction": {"launches": gst.launches, "ms": gst.ms, "share_of_step": gst.ms / ms_m,
                                 "tensor_tflops": tc_rate, "tensor_peak_tflops": tc_peak,
                                 "tensor_frac": tc_rate / tc_peak if tc_rate else None,
