@@ -394,6 +394,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--no-time-to-se", action="store_true")
     ap.add_argument("--table1", action="store_true",
                     help="per-sample std of Z~ on the paper's 128-spin network (Table 1) instead of the bench line")
     args = ap.parse_args()
@@ -608,11 +609,12 @@ def main():
             line["serve"] = measure_serving(mctrg, args.serve_seconds, args.serve_load)
         except Exception as e:
             line["serve"] = {"error": repr(e)[:200]}
-    try:
-        line["time_to_se_32x32"] = {"fp64": measure_time_to_se(mctrg, 0),
-                                    "fp64tc": measure_time_to_se(mctrg, mctrg.MCTRG_FP64TC)}
-    except Exception as e:
-        line["time_to_se_32x32"] = {"error": repr(e)[:200]}
+    if not args.no_time_to_se:
+        try:
+            line["time_to_se_32x32"] = {"fp64": measure_time_to_se(mctrg, 0),
+                                        "fp64tc": measure_time_to_se(mctrg, mctrg.MCTRG_FP64TC)}
+        except Exception as e:
+            line["time_to_se_32x32"] = {"error": repr(e)[:200]}
     if not args.no_uneven:
         try:
             line["uneven_batch"] = measure_uneven(mctrg)
