@@ -36,6 +36,54 @@ def site_tensor(beta, h):
     return T
 
 
+def impurity_tensor(beta, h):
+    """The site tensor with the site's spin inserted (the impurity of Sec. III's
+    partial traces): T_imp[l,u,r,d] = sum_s s e^{beta h s} W[s,l] W[s,u] W[s,r] W[s,d].
+    Replacing site i's tensor by it gives sum_sigma sigma_i e^{-beta H} = Z <sigma_i>."""
+    W = np.array([[math.sqrt(math.cosh(beta)), math.sqrt(math.sinh(beta))],
+                  [math.sqrt(math.cosh(beta)), -math.sqrt(math.sinh(beta))]])
+    T = np.zeros((2, 2, 2, 2))
+    for s, spin in enumerate((1.0, -1.0)):
+        w = W[s]
+        T += spin * math.exp(beta * h * spin) * np.einsum('a,b,c,d->abcd', w, w, w, w)
+    return T
+
+
+def brute_force_observable(L, beta, h, sites):
+    """<prod_{i in sites} sigma_i> and ln Z by enumerating every configuration;
+    a site is (x, y)."""
+    n = L * L
+    if n > 20:
+        raise ValueError("brute force limited to L*L <= 20")
+    idx = np.arange(1 << n, dtype=np.int64)
+    spins = (1 - 2 * ((idx[:, None] >> np.arange(n)) & 1)).reshape(-1, L, L)   # [state, y, x]
+    bonds = (spins * np.roll(spins, -1, axis=2)).sum(axis=(1, 2)) \
+        + (spins * np.roll(spins, -1, axis=1)).sum(axis=(1, 2))
+    e = beta * bonds + beta * h * spins.sum(axis=(1, 2))
+    w = np.exp(e - e.max())
+    obs = np.ones(len(idx))
+    for x, y in sites:
+        obs = obs * spins[:, y, x]
+    return float(np.sum(w * obs) / np.sum(w)), _logsumexp(e)
+
+
+def transfer_observable(L, beta, h, columns):
+    """<prod_{x in columns} sigma_(x, 0)> on the L x L torus (L <= 10) from the row
+    transfer matrix: Tr(S T^L) / Tr(T^L), S the diagonal of the product of the
+    row's spins at those columns (any row: translation invariance)."""
+    if L > 10:
+        raise ValueError("transfer matrix limited to L <= 10")
+    rows = list(itertools.product((1, -1), repeat=L))
+    R = np.array(rows, dtype=np.float64)
+    intra = (R * np.roll(R, -1, axis=1)).sum(axis=1)
+    field = R.sum(axis=1)
+    logT = beta * (R @ R.T) + beta * (intra + h * field)[:, None]
+    T = np.exp(logT - logT.max())
+    P = np.linalg.matrix_power(T / np.linalg.norm(T, 2), L)
+    S = np.prod(R[:, list(columns)], axis=1)
+    return float(np.sum(S * np.diag(P)) / np.trace(P))
+
+
 def _logsumexp(x):
     m = np.max(x)
     return float(m + np.log(np.sum(np.exp(x - m))))

@@ -96,7 +96,7 @@ def contract(F3, F4, F2, F1):
 class Problem:
     """A lattice: L x L torus of identical site tensors T0 (legs l,u,r,d)."""
 
-    def __init__(self, T0, L, chi, zero_tol_scale=1.0, deterministic_levels=0):
+    def __init__(self, T0, L, chi, zero_tol_scale=1.0, deterministic_levels=0, site_tensors=None):
         T0 = np.asarray(T0, dtype=np.float64)
         if T0.ndim != 4 or len(set(T0.shape)) != 1:
             raise ValueError("T0 must be D x D x D x D")
@@ -108,6 +108,9 @@ class Problem:
         self.n_levels = len(self.levels) - 1      # SVD levels: 0 .. 2m-1
         # levels 0 .. deterministic_levels-1 keep the chi largest values (Eq. approxSVD)
         self.deterministic_levels = int(deterministic_levels)
+        # {level-0 tensor id (y L + x): tensor} replacing T0 at those sites (impurities);
+        # such a network is not translation invariant: every level is split tensor by tensor
+        self.site_tensors = {int(k): np.asarray(v, dtype=np.float64) for k, v in (site_tensors or {}).items()}
 
 
 def _stochastic_chooser(seed, traj, level, tensor, chi, zero_scale=1.0):
@@ -180,7 +183,9 @@ def run_level(prob, k, tensors, shared, chooser_for, deterministic=False):
 def run_trajectory(prob, seed, traj):
     """One Monte Carlo trajectory -> (sign, ln|Z~|, flags)."""
     tensors = [prob.T0] * prob.levels[0].n
-    shared = True
+    for t, T in prob.site_tensors.items():
+        tensors[t] = T
+    shared = not prob.site_tensors
     lnacc = 0.0
     flags = 0
     for k in range(prob.n_levels):
