@@ -182,6 +182,27 @@ int mctrg_init_lattice(mctrg_ctx_t ctx, double beta, double h, int L, int chi);
  * Arguments, limits and errors as mctrg_init_lattice. */
 int mctrg_init_bond_lattice(mctrg_ctx_t ctx, double beta, double h, int L, int chi);
 
+/* Observables by impurity tensors (Sec. III: the method applies to partial
+ * traces as to Z).  The lattice of mctrg_init_lattice with the tensor of site
+ * (0, 0) -- and of its right neighbour (1, 0) when n_imp = 2 -- replaced by
+ * the site tensor with the site's spin inserted,
+ *   T_imp[l,u,r,d] = sum_s s e^{beta h s} W[s,l] W[s,u] W[s,r] W[s,d],
+ * so that every trajectory is an unbiased sample of Z <sigma_00> (n_imp = 1)
+ * or of Z <sigma_00 sigma_10> (n_imp = 2, the bond energy); signs are tracked
+ * as for Z.  The network is not translation invariant, so every level is
+ * split tensor by tensor from level 0 (leg dimensions min(chi, D^2) from
+ * D = 2, no shared prefix).  Divide by an estimate of Z with
+ * mctrg_ratio_estimate.  n_imp is 1 or 2; deterministic_levels must be 0.
+ * Errors: EINVAL, ECUDA. */
+int mctrg_init_impurity(mctrg_ctx_t ctx, double beta, double h, int L, int chi, int n_imp);
+
+/* Ratio of the means of two estimates from independent trajectory sets
+ * (e.g. Z <sigma> over Z), and its standard error by first-order error
+ * propagation (sum of the squared relative errors; an exactly zero numerator
+ * mean takes its own spread).  Host only.  Errors: EINVAL (n < 2), EDOMAIN
+ * (denominator mean <= 0). */
+int mctrg_ratio_estimate(const mctrg_estimate* num, const mctrg_estimate* den, double* ratio, double* se);
+
 /* Same as mctrg_init_lattice with an arbitrary site tensor T0 (host pointer,
  * D^4 doubles, index order [l][u][r][d], row-major), 1 <= D <= 8, copied. */
 int mctrg_init_tensor(mctrg_ctx_t ctx, const double* T0, int D, int L, int chi);

@@ -11,6 +11,7 @@
 //   T' = X Yt^T  (a GEMM with M = N = D^2, K = d^2).
 // Parent halves come from the level-k layout of the sampler: left [d^2][D]
 // (F1 of an A tensor, F2 of a B tensor), right [D][d^2] (F3 / F4).
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -201,6 +202,57 @@ __global__ void k_site_tensor(double beta, double h, double* T) {
 
 cudaError_t launch_site_tensor(double beta, double h, double* T, cudaStream_t st) {
   k_site_tensor<<<1, 32, 0, st>>>(beta, h, T);
+  return cudaGetLastError();
+}
+
+// The site tensor with the site's spin inserted (an impurity: the network's
+// trace becomes sum_sigma sigma_i e^{-beta H}, a partial trace of Sec. III):
+// T_imp[l,u,r,d] = sum_s s e^{beta h s} W[s,l] W[s,u] W[s,r] W[s,d].
+__global__ void k_impurity_tensor(double beta, double h, double* T) {
+  const int e = threadIdx.x;
+  if (e >= 16) return;
+  const int l = (e >> 3) & 1, u = (e >> 2) & 1, r = (e >> 1) & 1, d = e & 1;
+  const double c = sqrt(cosh(beta)), s = sqrt(sinh(beta));
+  double v = 0.0;
+  for (int k = 0; k < 2; ++k) {
+    const double spin = k == 0 ? 1.0 : -1.0;
+    const double w1 = spin * s;
+    const double wl = l ? w1 : c, wu = u ? w1 : c, wr = r ? w1 : c, wd = d ? w1 : c;
+    v += spin * exp(beta * h * spin) * (wl * wu * wr * wd);
+  }
+  T[e] = v;
+}
+
+cudaError_t launch_impurity_tensor(double beta, double h, double* T, cudaStream_t st) {
+  k_impurity_tensor<<<1, 32, 0, st>>>(beta, h, T);
+  return cudaGetLastError();
+}
+
+// Level-0 matrices of a network that is not translation invariant: item
+// item0 + it = b N0 + t takes site t's tensor (the impurity at sites imp0 /
+// imp1, the plain one elsewhere; D = 2), matricized by t's sublattice.
+__global__ void k_level0_matrices(const double* T0, const double* Timp, int imp0, int imp1, int L,
+                                  int64_t item0, int64_t n_items, int64_t N0, double* M) {
+  const int64_t tot = n_items * 16;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t it = e >> 4;
+    const int q = (int)(e & 15);
+    const int64_t t = (item0 + it) % N0;
+    const double* T = (t == imp0 || t == imp1) ? Timp : T0;
+    const int l = (q >> 3) & 1, u = (q >> 2) & 1, r = (q >> 1) & 1, d = q & 1;
+    const int par = tensor_parity(L, 0, t);
+    double* Mo = M + it * 16;
+    if (par == 0) Mo[(l * 2 + u) * 4 + (r * 2 + d)] = T[q];      // A: (l,u),(r,d)
+    else Mo[(u * 2 + r) * 4 + (d * 2 + l)] = T[q];               // B: (u,r),(d,l)
+  }
+}
+
+cudaError_t launch_level0_matrices(const double* T0, const double* Timp, int imp0, int imp1, int L, int64_t item0,
+                                   int64_t n_items, int64_t N0, double* M, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  const int64_t tot = n_items * 16;
+  const int64_t blocks = std::min<int64_t>((tot + 255) / 256, 4096);
+  k_level0_matrices<<<(unsigned)blocks, 256, 0, st>>>(T0, Timp, imp0, imp1, L, item0, n_items, N0, M);
   return cudaGetLastError();
 }
 

@@ -109,6 +109,12 @@ cudaError_t launch_site_tensor(double beta, double h, double* T, cudaStream_t st
 // The spins-on-bonds tensor of the paper's Fig. 1 network (D = 2).
 cudaError_t launch_bond_tensor(double beta, double h, double* T, cudaStream_t st);
 // A and B matricizations of a raw tensor T[l][u][r][d] (D^4): out[0] = A, out[1] = B.
+// The impurity tensor (site tensor with the site's spin inserted), D = 2.
+cudaError_t launch_impurity_tensor(double beta, double h, double* T, cudaStream_t st);
+// Level-0 matrices [n_items][4][4] of items item0.. (b N0 + t): site t's tensor
+// (Timp at imp0 / imp1, T0 elsewhere) matricized by its sublattice.
+cudaError_t launch_level0_matrices(const double* T0, const double* Timp, int imp0, int imp1, int L, int64_t item0,
+                                   int64_t n_items, int64_t N0, double* M, cudaStream_t st);
 cudaError_t launch_matricize2(const double* T, int D, double* out, cudaStream_t st);
 // lnacc[b] += sum_t ilns1[b*N+t] (if ilns1), tflags[b] |= OR_t iflags[b*N+t].
 cudaError_t launch_traj_accum(const double* ilns1, const uint32_t* iflags, int64_t N, int64_t B,

@@ -165,7 +165,7 @@ size_t mctrg_ctx::held_bytes() const {
   const DevBuf* all[] = {&T0, &shM, &shW, &shSig, &shPerm, &shNnz, &shLns1, &shU, &shH, &Hbuf[0], &Hbuf[1],
                          &Mb, &Wb, &Xb, &Yb, &sigb, &permb, &nnzb, &ilns1, &iflags, &lnacc, &tflags,
                          &scratch, &o_lnabs, &o_sign, &o_flags, &o_tflags, &stats, &tcXh, &tcYh, &tcXl,
-                         &tcYl, &tcScale, &tcErr, &ozExp, &bdb, &keptb, &sigtb, &nkb, &vrowsb, &bdscr};
+                         &tcYl, &tcScale, &tcErr, &ozExp, &Timp, &bdb, &keptb, &sigtb, &nkb, &vrowsb, &bdscr};
   size_t b = 0;
   for (const DevBuf* d : all) b += d->bytes;
   return b;
@@ -178,7 +178,7 @@ void mctrg_ctx::release_all() {
   DevBuf* all[] = {&T0, &shM, &shW, &shSig, &shPerm, &shNnz, &shLns1, &shU, &shH, &Hbuf[0], &Hbuf[1],
                    &Mb, &Wb, &Xb, &Yb, &sigb, &permb, &nnzb, &ilns1, &iflags, &lnacc, &tflags,
                    &scratch, &o_lnabs, &o_sign, &o_flags, &o_tflags, &stats, &tcXh, &tcYh, &tcXl,
-                   &tcYl, &tcScale, &tcErr, &ozExp, &bdb, &keptb, &sigtb, &nkb, &vrowsb, &bdscr};
+                   &tcYl, &tcScale, &tcErr, &ozExp, &Timp, &bdb, &keptb, &sigtb, &nkb, &vrowsb, &bdscr};
   for (DevBuf* b : all) b->release();
 }
 
@@ -197,6 +197,8 @@ int mctrg_ctx::init_from_device_tensor(int D0, int L_, int chi_) {
   s0 = nlev;
   all_exact = false;
   prefix_flags = 0;
+  level0_distinct = false;
+  imp0 = imp1 = -1;
   int D = D0;
   // cur raw tensor lives in T0 (D^4); the plaquette result goes to shM scratch then back
   for (int k = 0; k < nlev; ++k) {
@@ -332,6 +334,58 @@ extern "C" int mctrg_init_bond_lattice(mctrg_ctx_t c, double beta, double h, int
   return c->init_from_device_tensor(2, L, chi);
 }
 
+extern "C" int mctrg_init_impurity(mctrg_ctx_t c, double beta, double h, int L, int chi, int n_imp) {
+  if (!c) return MCTRG_EINVAL;
+  if (!is_pow2(L) || L > 65536 || chi < 1 || chi > 32 || !(beta >= 0.0) || !std::isfinite(beta) ||
+      !std::isfinite(h) || (n_imp != 1 && n_imp != 2) || c->opt.deterministic_levels > 0)
+    return MCTRG_EINVAL;
+  CK(cudaSetDevice(c->opt.device));
+  c->ready = false;
+  CK(c->T0.ensure(16 * sizeof(double)));
+  CK(c->Timp.ensure(16 * sizeof(double)));
+  CK(launch_site_tensor(beta, h, c->T0.as<double>(), c->st));
+  CK(launch_impurity_tensor(beta, h, c->Timp.as<double>(), c->st));
+  // every level split per tensor from level 0: D' = min(chi, D^2) from D = 2
+  c->L = L;
+  c->chi = chi;
+  int m = 0;
+  while ((1 << m) < L) ++m;
+  c->nlev = 2 * m;
+  c->lv.clear();
+  int D = 2;
+  for (int k = 0; k < c->nlev; ++k) {
+    const int n = D * D;
+    c->lv.push_back(LevelInfo{level_count(L, k), D, n, n + (n & 1), std::min(chi, n)});
+    D = std::min(chi, n);
+  }
+  c->s0 = 0;
+  c->lnacc0 = 0.0;
+  c->all_exact = false;
+  c->prefix_flags = 0;
+  c->level0_distinct = true;
+  c->imp0 = 0;                       // site (0, 0)
+  c->imp1 = n_imp == 2 ? 1 : -1;     // site (1, 0), its right neighbour
+  CK(cudaStreamSynchronize(c->st));
+  c->ready = true;
+  return MCTRG_OK;
+}
+
+extern "C" int mctrg_ratio_estimate(const mctrg_estimate* num, const mctrg_estimate* den, double* ratio,
+                                    double* se) {
+  if (!num || !den || !ratio || num->n < 2 || den->n < 2) return MCTRG_EINVAL;
+  if (!(den->mean_Z_scaled > 0.0)) return MCTRG_EDOMAIN;
+  const double r = std::exp(num->ln_scale - den->ln_scale) * num->mean_Z_scaled / den->mean_Z_scaled;
+  *ratio = r;
+  if (se) {
+    const double a = num->mean_Z_scaled != 0.0 ? num->se_Z_scaled / num->mean_Z_scaled : INFINITY;
+    const double b = den->se_Z_scaled / den->mean_Z_scaled;
+    *se = std::fabs(r) * std::sqrt(a * a + b * b);
+    if (num->mean_Z_scaled == 0.0)   // an exactly zero numerator: the SE from its spread alone
+      *se = std::exp(num->ln_scale - den->ln_scale) * num->se_Z_scaled / den->mean_Z_scaled;
+  }
+  return MCTRG_OK;
+}
+
 extern "C" int mctrg_init_tensor(mctrg_ctx_t c, const double* T0, int D, int L, int chi) {
   if (!c || !T0) return MCTRG_EINVAL;
   if (!is_pow2(L) || L > 65536 || chi < 1 || chi > 32 || D < 1 || D > 8) return MCTRG_EINVAL;
@@ -395,6 +449,11 @@ void plan_run(const std::vector<LevelInfo>& lv, int s0, int nlev, int chi, const
     per_traj += fin;
   }
   per_traj += max_pair + max_items * (sizeof(double) + sizeof(uint32_t));
+  {  // level s0 split per item (a lattice with impurities): its matrices, rows and values
+    const LevelInfo& a = lv[s0];
+    per_item = std::max(per_item, ((size_t)a.n * a.n + (size_t)a.n_pad * a.n + a.n_pad) * sizeof(double) +
+                                      (a.n_pad + 1) * sizeof(int) + sizeof(double) + sizeof(uint32_t));
+  }
   const size_t tables = sample_scratch_doubles(lv[nlev - 1].n, chi, 1024) * sizeof(double) + bd_scr;
   const int64_t Bmax = opt.max_chunk > 0 ? std::min<int64_t>(opt.max_chunk, n_samples) : n_samples;
   const size_t work_budget = std::max<size_t>(budget / 4, 1);
@@ -524,6 +583,13 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
       const LevelInfo& a = lv[nlev - 1];
       max_xy = std::max(max_xy, (size_t)B * a.kc * a.kc * a.n);
     }
+    if (level0_distinct) {   // level 0's own matrices, SVD and sampling per item
+      const LevelInfo& a = lv[0];
+      max_m = std::max(max_m, (size_t)S * a.n * a.n);
+      max_w = std::max(max_w, (size_t)S * a.n_pad * a.n);
+      max_np = std::max(max_np, (size_t)S * a.n_pad);
+      max_items = std::max(max_items, (size_t)B * a.N);
+    }
     CK(Hbuf[0].ensure(sizeof(double) * max_h));
     CK(Hbuf[1].ensure(sizeof(double) * max_h));
     CK(iflags.ensure(sizeof(uint32_t) * max_items));
@@ -595,7 +661,37 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
       CK(cudaMemsetAsync(lnacc.p, 0, sizeof(double) * Bc, st));
       CK(cudaMemsetAsync(o_tflags.p, 0, sizeof(uint32_t) * Bc, st));
       int cur = 0;
-      {  // level s0: shared SVD, per-(trajectory, tensor) sampling
+      if (level0_distinct) {  // level 0 of a lattice with impurities: every tensor split on its own
+        const LevelInfo& a = lv[0];
+        const int64_t items = Bc * a.N;
+        CK(cudaMemsetAsync(iflags.p, 0, sizeof(uint32_t) * items, st));
+        for (int64_t i0 = 0; i0 < items; i0 += S) {
+          const int64_t Si = std::min(S, items - i0);
+          CK(timed(MCTRG_K_OTHER, Si, 0.0, 8.0 * Si * a.n * a.n, [&] {
+            return launch_level0_matrices(T0.as<double>(), Timp.as<double>(), imp0, imp1, L, i0, Si, a.N,
+                                          Mb.as<double>(), st); }));
+          JacobiArgs ja{};
+          ja.M = Mb.as<double>(); ja.W = Wb.as<double>(); ja.sig = sigb.as<double>();
+          ja.perm = permb.as<int>(); ja.lns1 = ilns1.as<double>() + i0; ja.nnz = nnzb.as<int>();
+          ja.mflags = iflags.as<uint32_t>() + i0; ja.n = a.n; ja.n_pad = a.n_pad; ja.S = (int)Si;
+          ja.max_sweeps = opt.max_sweeps;
+          ja.zero_rel = opt.zero_tol_scale * (double)a.n * 0x1.0p-52;
+          const double nn = a.n;
+          CK(timed(MCTRG_K_JACOBI, Si, Si * ((8.0 / 3.0) * nn * nn * nn + 4.0 * nn * nn * a.kc),
+                   8.0 * Si * (nn * nn + (double)a.n_pad * nn + 1.5 * a.n_pad), [&] { return launch_jacobi(ja, st); }));
+          SampleArgs sa{};
+          sa.M = Mb.as<double>(); sa.W = Wb.as<double>(); sa.sig = sigb.as<double>(); sa.perm = permb.as<int>();
+          sa.nnz = nnzb.as<int>(); sa.Urows = nullptr; sa.n = a.n; sa.n_pad = a.n_pad; sa.chi = chi; sa.kc = a.kc;
+          sa.stochastic = 1; sa.shared_svd = 0; sa.item0 = i0; sa.n_items = Si; sa.N = a.N; sa.L = L; sa.level = 0;
+          sa.seed = seed; sa.traj0 = traj0; sa.H = Hbuf[cur].as<double>(); sa.h_item0 = 0;
+          sa.iflags = iflags.as<uint32_t>(); sa.scratch = scratch.as<double>(); sa.mode = 0;
+          CK(timed(MCTRG_K_SAMPLE, Si, Si * (4.0 * nn * a.kc + 2.0 * nn * nn * a.kc),
+                   8.0 * Si * (2.0 * nn * nn + 2.0 * nn * a.kc), [&] { return launch_sample_split(sa, st, grid_s); }));
+        }
+        CK(timed(MCTRG_K_OTHER, Bc, 0.0, 12.0 * items, [&] {
+          return launch_traj_accum(ilns1.as<double>(), iflags.as<uint32_t>(), a.N, Bc, lnacc.as<double>(),
+                                   o_tflags.as<uint32_t>(), st); }));
+      } else {  // level s0: shared SVD, per-(trajectory, tensor) sampling
         const LevelInfo& a = lv[s0];
         const int64_t items = Bc * a.N;
         CK(cudaMemsetAsync(iflags.p, 0, sizeof(uint32_t) * items, st));

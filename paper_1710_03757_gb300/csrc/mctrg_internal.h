@@ -49,6 +49,10 @@ struct mctrg_ctx {
   double lnacc0 = 0.0;      // sum of ln s_1 over the shared levels 0..s0
   bool all_exact = false;
   uint32_t prefix_flags = 0; // flags of the shared levels (deterministic truncations), in every trajectory
+  // impurity lattices: every level split per tensor from level 0 (no shared
+  // prefix); sites imp0 / imp1 (-1: none) hold the tensor Timp instead of T0
+  bool level0_distinct = false;
+  int imp0 = -1, imp1 = -1;
   double const_lnabs = 0.0;
   int const_sign = 0;
   mctrg::DevBuf T0, shM, shW, shSig, shPerm, shNnz, shLns1, shU, shH;
@@ -56,6 +60,7 @@ struct mctrg_ctx {
   mctrg::DevBuf o_lnabs, o_sign, o_flags, o_tflags, stats;
   mctrg::DevBuf tcXh, tcYh, tcXl, tcYl, tcScale, tcErr;   // tensor-core operands (slice planes in FP64TC)
   mctrg::DevBuf ozExp;                                     // FP64TC: row exponents of X and Yt
+  mctrg::DevBuf Timp;                                      // impurity tensor (level0_distinct)
   mctrg::DevBuf bdb, keptb, sigtb, nkb, vrowsb, bdscr;    // bidiagonalization route
 
   // per-kernel-class statistics (MCTRG_K_*)

@@ -24,7 +24,8 @@ EXPORTS = [
     "mctrg_server_destroy", "mctrg_plan_level", "mctrg_philox_uniform", "mctrg_kernel_stats",
     "mctrg_reset_kernel_stats", "mctrg_svd_batched", "mctrg_svd_batched_noalloc",
     "mctrg_svd_bidiag_batched", "mctrg_measure_fp64_peak", "mctrg_contract_batched",
-    "mctrg_server_footprint", "mctrg_server_memory", "mctrg_batch_run",
+    "mctrg_server_footprint", "mctrg_server_memory", "mctrg_batch_run", "mctrg_init_impurity",
+    "mctrg_ratio_estimate",
 ]
 K_FORM_XY, K_GEMM, K_JACOBI, K_SAMPLE, K_TRACE, K_OTHER, K_BIDIAG, K_BISECT, K_VECTORS, K_COUNT = range(10)
 KERNEL_NAMES = ["form_xy", "gemm", "jacobi", "sample_split", "trace", "other", "bidiag", "bisect", "vectors"]
@@ -79,6 +80,9 @@ def lib():
             "mctrg_init_lattice": (c_int, [vp, c_double, c_double, c_int, c_int]),
             "mctrg_init_bond_lattice": (c_int, [vp, c_double, c_double, c_int, c_int]),
             "mctrg_init_tensor": (c_int, [vp, vp, c_int, c_int, c_int]),
+            "mctrg_init_impurity": (c_int, [vp, c_double, c_double, c_int, c_int, c_int]),
+            "mctrg_ratio_estimate": (c_int, [ctypes.POINTER(Estimate), ctypes.POINTER(Estimate),
+                                             ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
             "mctrg_run": (c_int, [vp, i64, u64, u64, vp, vp, vp, ctypes.POINTER(Estimate)]),
             "mctrg_footprint": (c_int, [vp, i64, ctypes.POINTER(ctypes.c_size_t)]),
             "mctrg_merge_estimates": (c_int, [ctypes.POINTER(Estimate), c_int, ctypes.POINTER(Estimate)]),
@@ -176,6 +180,18 @@ def mctrg_init_lattice(ctx, beta, h, L, chi):
 def mctrg_init_bond_lattice(ctx, beta, h, L, chi):
     """The spins-on-bonds network of the paper's Fig. 1 (L = 8: 128 spins)."""
     return lib().mctrg_init_bond_lattice(ctx, float(beta), float(h), int(L), int(chi))
+
+
+def mctrg_init_impurity(ctx, beta, h, L, chi, n_imp=1):
+    """Site (0,0) (and (1,0) for n_imp = 2) carries its spin: trajectories sample Z <sigma ...>."""
+    return lib().mctrg_init_impurity(ctx, float(beta), float(h), int(L), int(chi), int(n_imp))
+
+
+def mctrg_ratio_estimate(num, den):
+    """(status, ratio, standard error) of two estimates' means."""
+    r, se = ctypes.c_double(), ctypes.c_double()
+    s = lib().mctrg_ratio_estimate(ctypes.byref(num), ctypes.byref(den), ctypes.byref(r), ctypes.byref(se))
+    return s, r.value, se.value
 
 
 def mctrg_init_tensor(ctx, T0, D, L, chi):

@@ -113,3 +113,26 @@ def test_create_rejects_bad_options_before_touching_the_device():
         o = mctrg.make_options(**bad)
         assert lib.mctrg_create(ctypes.byref(o), ctypes.byref(h)) == mctrg.MCTRG_EINVAL, bad
     assert lib.mctrg_create(None, ctypes.byref(h)) == mctrg.MCTRG_EINVAL
+
+
+def test_ratio_estimate_matches_first_order_propagation():
+    # two estimates from the oracle's estimator on synthetic per-trajectory values
+    rng = np.random.default_rng(3)
+    parts = []
+    for shift in (0.0, 2.5):
+        ln = rng.normal(10.0 + shift, 0.3, 500)
+        sg = np.ones(500, np.int8)
+        e = mctrg.Estimate()
+        ref = estimate(sg, ln)
+        x = np.exp(ln - ref['ln_scale'])
+        e.n, e.ln_scale, e.mean_Z_scaled, e.se_Z_scaled = 500, ref['ln_scale'], x.mean(), x.std(ddof=1) / math.sqrt(500)
+        parts.append((e, np.exp(ln)))
+    st, r, se = mctrg.mctrg_ratio_estimate(parts[1][0], parts[0][0])
+    assert st == 0
+    a, b = parts[1][1], parts[0][1]
+    exp_r = a.mean() / b.mean()
+    exp_se = exp_r * math.hypot(a.std(ddof=1) / math.sqrt(500) / a.mean(), b.std(ddof=1) / math.sqrt(500) / b.mean())
+    assert r == pytest.approx(exp_r, rel=1e-12) and se == pytest.approx(exp_se, rel=1e-10)
+    bad = mctrg.Estimate()
+    bad.n, bad.mean_Z_scaled = 10, -1.0
+    assert mctrg.mctrg_ratio_estimate(parts[0][0], bad)[0] == mctrg.MCTRG_EDOMAIN
