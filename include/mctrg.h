@@ -128,7 +128,8 @@ typedef struct {
  *           (8/3) n^3 + O(n^2) flops whatever the rank.
  *   AUTO    BIDIAG where the matrices can have full rank (n >= 64 and the
  *           plaquette's inner dimension d^2 >= n / 2), JACOBI elsewhere.
- * BIDIAG covers n <= 1024 (chi <= 32); larger levels take JACOBI. */
+ * JACOBI covers n <= 1024: levels with larger matrices (n up to 2304, chi up
+ * to 48) take BIDIAG whatever the option. */
 typedef enum { MCTRG_SVD_AUTO = 0, MCTRG_SVD_JACOBI = 1, MCTRG_SVD_BIDIAG = 2 } mctrg_svd_route;
 
 /* Estimate of Z from n trajectories (Sec. III Eq. infiniteEnsemble, Sec. V Eq.
@@ -165,7 +166,7 @@ int mctrg_create(const mctrg_options* opt, mctrg_ctx_t* out);
 
 /* Set up an L x L periodic Ising lattice at inverse temperature beta >= 0 and
  * field h (Sec. IV), truncating every SVD to chi kept singular values
- * (Sec. II).  L must be a power of two, 2 <= L <= 65536; 1 <= chi <= 32.
+ * (Sec. II).  L must be a power of two, 2 <= L <= 65536; 1 <= chi <= 48.
  * The site tensor is T[l,u,r,d] = sum_s e^{beta h s} W[s,l] W[s,u] W[s,r] W[s,d]
  * with W[s,0] = sqrt(cosh beta), W[s,1] = s sqrt(sinh beta).  Runs the shared
  * deterministic prefix (levels where nothing is sampled, and the one SVD of
@@ -361,7 +362,7 @@ int mctrg_contract_batched(const double* X, const double* Yt, int D, int K, int6
  * cluster's subspace; vectors of values at the noise level (a few 2^-52 n |M|
  * and below: the numerical null space) are not determined and carry no
  * guarantee.  Allocates and frees its working memory.
- * 2 <= n <= 1024, 0 <= n_vec <= min(32, n).  Errors: EINVAL, ENOMEM, ECUDA. */
+ * 2 <= n <= 2304, 0 <= n_vec <= min(64, n).  Errors: EINVAL, ENOMEM, ECUDA. */
 int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, double* sigma, int n_vec,
                              double* vt, void* stream);
 

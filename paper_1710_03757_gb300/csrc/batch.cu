@@ -143,10 +143,11 @@ ItemLayout layout(const mctrg_ctx* c, int k, int prec) {
   L.sig = np * sizeof(double);
   L.perm = np * sizeof(int);
   L.nnz = sizeof(int);
-  L.kept = 32 * sizeof(int);
-  L.sigt = 32 * sizeof(double);
+  const size_t ks = kept_stride(c->chi);
+  L.kept = ks * sizeof(int);
+  L.sigt = ks * sizeof(double);
   L.nk = sizeof(int);
-  L.vrows = 32 * n * sizeof(double);
+  L.vrows = ks * n * sizeof(double);
   L.oz = (prec == MCTRG_FP64TC && gemm_ozaki_supported((int)n, (int)d2)) ? 8 * n * d2 * 2 : 0;
   L.ozexp = L.oz ? n * sizeof(int) : 0;
   L.total = 2 * L.x + L.m + L.w + L.bd + L.sig + L.perm + L.nnz + L.kept + L.sigt + L.nk + L.vrows + 2 * L.oz +
@@ -232,7 +233,8 @@ struct BatchRunner {
     BCK(c->o_tflags.ensure(sizeof(uint32_t) * B));
     BCK(c->Xb.ensure(sizeof(double) * (size_t)B * fl.kc * fl.kc * fl.n));
     BCK(c->Yb.ensure(sizeof(double) * (size_t)B * fl.kc * fl.kc * fl.n));
-    BCK(c->scratch.ensure(sizeof(double) * sample_scratch_doubles(c->lv[c->s0].n, c->chi, 1024)));
+    const int g0 = sample_grid(c->lv[c->s0].n, c->chi);
+    BCK(c->scratch.ensure(sizeof(double) * sample_scratch_doubles(c->lv[c->s0].n, c->chi, g0)));
     BCK(cudaMemsetAsync(c->lnacc.p, 0, sizeof(double) * B, st));
     BCK(cudaMemsetAsync(c->o_tflags.p, 0, sizeof(uint32_t) * B, st));
     const LevelInfo& a = c->lv[c->s0];
@@ -245,7 +247,7 @@ struct BatchRunner {
     sa.item0 = 0; sa.n_items = items; sa.N = a.N; sa.L = c->L; sa.level = c->s0; sa.seed = r.job.seed;
     sa.traj0 = r.job.first_traj; sa.H = c->Hbuf[0].as<double>(); sa.h_item0 = 0;
     sa.iflags = c->iflags.as<uint32_t>(); sa.scratch = c->scratch.as<double>();
-    BCK(launch_sample_split(sa, st, 1024));
+    BCK(launch_sample_split(sa, st, g0));
     BCK(launch_traj_accum(nullptr, c->iflags.as<uint32_t>(), a.N, B, c->lnacc.as<double>(),
                           c->o_tflags.as<uint32_t>(), st));
     launches += 2;
@@ -294,7 +296,7 @@ struct BatchRunner {
   TuneVal tuned(int n, int kc) const {
     auto it = tune.find(TuneKey{n, kc});
     if (it != tune.end()) return it->second;
-    return TuneVal{1 << 16, 1024};
+    return TuneVal{1 << 16, sample_grid(n, kc)};
   }
 
   // ---- one sub-batch ---------------------------------------------------------
@@ -389,8 +391,9 @@ struct BatchRunner {
           SvdItem t{};
           t.M = q.M + (size_t)i * a.n * a.n; t.W = q.W + (size_t)i * a.n_pad * a.n; t.bd = q.bd + (size_t)i * 3 * a.n;
           t.sig = q.sig + (size_t)i * a.n_pad; t.perm = q.perm + (size_t)i * a.n_pad; t.nnz = q.nnz + i;
-          t.lns1 = c->ilns1.as<double>() + g.i0 + i; t.kept = q.kept + (size_t)i * 32; t.nk = q.nk + i;
-          t.vrows = q.vrows + (size_t)i * 32 * a.n; t.zero_rel = zero_fp64(a.n); t.n = a.n; t.n_pad = a.n_pad;
+          const size_t ks = kept_stride(c->chi);
+          t.lns1 = c->ilns1.as<double>() + g.i0 + i; t.kept = q.kept + (size_t)i * ks; t.nk = q.nk + i;
+          t.vrows = q.vrows + (size_t)i * ks * a.n; t.zero_rel = zero_fp64(a.n); t.n = a.n; t.n_pad = a.n_pad;
           items.push_back(t);
           item_n.push_back(a.n);
         }
@@ -433,7 +436,7 @@ struct BatchRunner {
           ++launches;
         }
       BCK(join(used) == MCTRG_OK ? cudaSuccess : cudaErrorUnknown);
-      const size_t vneed = sizeof(double) * bd_vectors_scratch_doubles(n_max, std::min(S, chunk));
+      const size_t vneed = sizeof(double) * bd_vectors_scratch_doubles(n_max, std::min(S, chunk), kmax);
       if (vneed > vec_scr.bytes) BCK(cudaStreamSynchronize(st));
       BCK(vec_scr.ensure(vneed));
       for (int i0 = 0; i0 < S; i0 += chunk) {
@@ -467,6 +470,7 @@ struct BatchRunner {
     sa.traj0 = r.job.first_traj; sa.H = c->Hbuf[r.cur].as<double>(); sa.h_item0 = 0;
     sa.iflags = c->iflags.as<uint32_t>(); sa.scratch = smp_scr.as<double>() + (s % kStreams) * smp_region;
     sa.mode = mode;
+    sa.kstride = kept_stride(c->chi);
     if (mode == 0) { sa.W = q.W; }
     else { sa.W = nullptr; sa.kept = q.kept; sa.sigt = q.sigt; sa.nk = q.nk; sa.vrows = q.vrows; }
     return sa;
@@ -486,7 +490,8 @@ struct BatchRunner {
     const int np = n + (n & 1);
     const int cands[5] = {1, 2, 4, 8, 16};
     // test matrices: up to 16 per SM, within 2 GB
-    const size_t per_mat = ((size_t)2 * np * n + 4 * (size_t)n + 32 * (size_t)n) * sizeof(double);
+    const int ks = kept_stride(kc);
+    const size_t per_mat = ((size_t)2 * np * n + 4 * (size_t)n + (size_t)ks * n) * sizeof(double);
     const int total = (int)std::max<size_t>(sms, std::min<size_t>(16 * (size_t)sms, ((size_t)2 << 30) / per_mat));
     OwnedBuf M, W, bd, sig, perm, nnz, l1, vr, kept, nk, scr, tab;
     BCK(M.ensure(sizeof(double) * (size_t)total * n * n));
@@ -496,14 +501,14 @@ struct BatchRunner {
     BCK(perm.ensure(sizeof(int) * (size_t)total * np));
     BCK(nnz.ensure(sizeof(int) * total));
     BCK(l1.ensure(sizeof(double) * total));
-    BCK(kept.ensure(sizeof(int) * 32 * (size_t)total));
+    BCK(kept.ensure(sizeof(int) * ks * (size_t)total));
     BCK(nk.ensure(sizeof(int) * total));
-    BCK(vr.ensure(sizeof(double) * 32 * (size_t)total * n));
+    BCK(vr.ensure(sizeof(double) * ks * (size_t)total * n));
     k_fill_random<<<1024, 256, 0, st>>>(M.as<double>(), (int64_t)total * n * n, 0x7E57ull);
     BCK(cudaGetLastError());
-    std::vector<int> hk(32 * (size_t)total), hn(total, kc);
+    std::vector<int> hk(ks * (size_t)total), hn(total, kc);
     for (int i = 0; i < total; ++i)
-      for (int q = 0; q < 32; ++q) hk[(size_t)i * 32 + q] = q < kc ? q : 0;
+      for (int q = 0; q < ks; ++q) hk[(size_t)i * ks + q] = q < kc ? q : 0;
     BCK(cudaMemcpyAsync(kept.p, hk.data(), sizeof(int) * hk.size(), cudaMemcpyHostToDevice, st));
     BCK(cudaMemcpyAsync(nk.p, hn.data(), sizeof(int) * hn.size(), cudaMemcpyHostToDevice, st));
     std::vector<SvdItem> its(total);
@@ -512,12 +517,12 @@ struct BatchRunner {
       t.M = M.as<double>() + (size_t)i * n * n; t.W = W.as<double>() + (size_t)i * np * n;
       t.bd = bd.as<double>() + (size_t)i * 3 * n; t.sig = sig.as<double>() + (size_t)i * np;
       t.perm = perm.as<int>() + (size_t)i * np; t.nnz = nnz.as<int>() + i; t.lns1 = l1.as<double>() + i;
-      t.kept = kept.as<int>() + (size_t)i * 32; t.nk = nk.as<int>() + i; t.vrows = vr.as<double>() + (size_t)i * 32 * n;
+      t.kept = kept.as<int>() + (size_t)i * ks; t.nk = nk.as<int>() + i; t.vrows = vr.as<double>() + (size_t)i * ks * n;
       t.zero_rel = zero_fp64(n); t.n = n; t.n_pad = np;
     }
     BCK(tab.ensure(sizeof(SvdItem) * its.size()));
     BCK(cudaMemcpyAsync(tab.p, its.data(), sizeof(SvdItem) * its.size(), cudaMemcpyHostToDevice, st));
-    BCK(scr.ensure(sizeof(double) * bd_vectors_scratch_doubles(n, total)));
+    BCK(scr.ensure(sizeof(double) * bd_vectors_scratch_doubles(n, total, kc)));
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));

@@ -1,6 +1,7 @@
 // Shared device/host helpers of the MC-TRG library: TRG geometry on the
 // torus, the Philox4x32-10 uniform stream, and error plumbing.
 #pragma once
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -123,6 +124,14 @@ inline cudaError_t raise_smem_limit(Kernel* kernel, int bytes, std::atomic<uint6
   if (e != cudaSuccess) return e;
   const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
   if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  // no more than the device allows a block beside the kernel's static shared memory
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  bytes = std::min(bytes, optin - (int)fa.sharedSizeBytes);
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
   return e;

@@ -230,6 +230,91 @@ struct BdDispatch<NQ + 1, NQ> {
   static __device__ __forceinline__ double fused(int, const BdStep&, double*) { return 0.0; }
 };
 
+// Wide form (sides above 1024, whose rows no longer fit in registers; the
+// matrix is in the global workspace): each step's fused pass sweeps a group of
+// R rows twice -- the first sweep forms a = A[i] - v_i w and y = a.us, the
+// second recomputes a, applies a -= y us, stores it and adds the next step's
+// column dots into this warp's row of wpart (shared memory; lane l owns the
+// columns k+1+l+32j throughout, so no other lane touches them).  One FMA per
+// element more than the register form; the same operations in the same order
+// otherwise.
+__device__ __forceinline__ void bdw_w_pass(const BdStep& s) {
+  constexpr int NW = kBdThreads / 32;
+  const int n = s.n, k = s.k;
+  double* wp = s.wpart + (size_t)s.warp * n;
+  for (int c = k + 1 + s.lane; c < n; c += 32) wp[c] = 0.0;
+  for (int i = k + 1 + s.warp; i < n; i += NW) {
+    const double vi = s.vcol[i];
+    const double* row = s.A + (size_t)i * n;
+    for (int c = k + 1 + s.lane; c < n; c += 32) wp[c] = fma(vi, row[c], wp[c]);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ double bdw_rows(const BdStep& s, int i0, double* vcol_out) {
+  const int n = s.n, k = s.k, lane = s.lane;
+  double vi[R];
+  double* row[R];
+  double y[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    vi[r] = s.vcol[i0 + r];
+    row[r] = s.A + (size_t)(i0 + r) * n;
+  }
+#pragma unroll 2
+  for (int c = k + 1 + lane; c < n; c += 32) {
+    const double wc = s.wv[c], uc = s.uv[c];
+#pragma unroll
+    for (int r = 0; r < R; ++r) y[r] = fma(fma(-vi[r], wc, row[r][c]), uc, y[r]);
+  }
+  const double t = reduce4(y[0], y[1], y[2], y[3], lane);
+  double yr[R], xm[R];
+  double nsq = 0.0;
+  const double wk = s.wv[k + 1], uk = s.uv[k + 1];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    yr[r] = __shfl_sync(0xffffffffu, t, 8 * r);
+    const int i = i0 + r;
+    // column k+1 of the updated row (every lane forms it; lane 0's sweep below
+    // writes the same value)
+    const double x = fma(-yr[r], uk, fma(-vi[r], wk, row[r][k + 1]));
+    if (lane == 0) {
+      vcol_out[i] = x;                           // column k+1 for the next step
+      if (i > k + 1) nsq = fma(x, x, nsq);
+    }
+    xm[r] = i > k + 1 ? x : 0.0;
+  }
+  __syncwarp();
+  double* wp = s.wpart + (size_t)s.warp * n;
+#pragma unroll 2
+  for (int c = k + 1 + lane; c < n; c += 32) {
+    const double wc = s.wv[c], uc = s.uv[c];
+    double acc = wp[c];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const double v = fma(-yr[r], uc, fma(-vi[r], wc, row[r][c]));
+      row[r][c] = v;
+      acc = fma(xm[r], v, acc);
+    }
+    wp[c] = acc;
+  }
+  return nsq;
+}
+
+__device__ __forceinline__ double bdw_fused_pass(const BdStep& s, double* vcol_out) {
+  constexpr int NW = kBdThreads / 32;
+  constexpr int RPW = 4;
+  const int n = s.n, k = s.k;
+  double* wp = s.wpart + (size_t)s.warp * n;
+  for (int c = k + 1 + s.lane; c < n; c += 32) wp[c] = 0.0;
+  double nsq = 0.0;
+  int i0 = k + 1 + RPW * s.warp;
+  for (; i0 + RPW <= n; i0 += RPW * NW) nsq += bdw_rows<RPW>(s, i0, vcol_out);
+  for (int i = i0; i < n && i < i0 + RPW; ++i) nsq += bdw_rows<1>(s, i, vcol_out);
+  return nsq;
+}
+
+// NQ > 0: the register form for sides up to 32 NQ; NQ = 0: the wide form.
 template <int NQ>
 __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_smem) {
   extern __shared__ double sm[];
@@ -242,7 +327,7 @@ __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_sme
   if (a.items) {                     // ragged: this matrix's size and buffers
     const SvdItem& t = a.items[mat];
     n = t.n; Mm = t.M; Wm = t.W; bd = t.bd;
-    use_smem = ((size_t)n * n + (size_t)(3 + NW) * n + 32) * sizeof(double) <= 200 * 1024;
+    use_smem = NQ > 0 && ((size_t)n * n + (size_t)(3 + NW) * n + 32) * sizeof(double) <= 200 * 1024;
   } else {
     Mm = a.M + (size_t)mat * n * n; Wm = a.W + (size_t)mat * n * n; bd = a.bd + (size_t)mat * 3 * n;
   }
@@ -272,7 +357,10 @@ __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_sme
   BdStep st{A, vcol, wv, uv, wpart, n, 0, lane, warp};
   // the column dots of step 0 with the unnormalized column 0: later steps get
   // theirs from the previous fused pass (w is linear in the column)
-  if (n > 1) BdDispatch<1, NQ>::w_pass((n - 1 + 31) >> 5, st);
+  if (n > 1) {
+    if constexpr (NQ == 0) bdw_w_pass(st);
+    else BdDispatch<1, NQ>::w_pass((n - 1 + 31) >> 5, st);
+  }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     st.k = k;
@@ -328,7 +416,9 @@ __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_sme
     if (tid == 0) { uv[k + 1] = sqrt(taur); bd[n + k] = betar; bd[2 * n + k] = taur; }
     __syncthreads();
     // ---- fused pass over rows i > k
-    const double nsq = BdDispatch<1, NQ>::fused(ql, st, vcol);
+    double nsq;
+    if constexpr (NQ == 0) nsq = bdw_fused_pass(st, vcol);
+    else nsq = BdDispatch<1, NQ>::fused(ql, st, vcol);
     __syncthreads();                            // everyone done with red / vcol reads
     if (lane == 0) red[warp] = nsq;
     __syncthreads();
@@ -353,8 +443,11 @@ __global__ void __launch_bounds__(kBdThreads) k_bidiag(BidiagArgs a, int use_sme
 //    det(T - x I) = P_2n = f 2^fe.  Four steps between checks of the pair's
 //    magnitude: after a check the larger of |P_k|, |P_{k-1}| is >= 2^-100, and
 //    four steps shrink it by at most 2^-416 (x >= 2^-53, one cancellation), so
-//    nothing underflows; growth is at most 2 per step (|T| <= 1), so nothing
-//    overflows in 2n <= 1536 steps.
+//    nothing underflows.  Unscaled, every P_k is at most about 1 in magnitude
+//    at any n (the eigenvalues of each leading block of the zero-diagonal T
+//    come in +- pairs within [-1, 1], so |P_k| <= prod |x^2 - l^2| <=
+//    (1 + 2^-20)^k for x <= 1 + 2^-20): the stored values exceed 1 only by the
+//    factors a rescaling put in.
 #define MCTRG_STURM_STEP(K)                                          \
   {                                                                  \
     double q = fma(-x, p, -oo[(K) - 2] * pp);                        \
@@ -583,15 +676,61 @@ __global__ void __launch_bounds__(kBisThreads) k_bd_bisect(const double* bd, int
 }
 
 // ---------------------------------------------------------------------------
-// 3. Inverse iteration, one warp per matrix (persistent over matrices), lane a
-//    for the a-th kept index.  Scratch per warp slot, interleaved by lane with
-//    stride ls (16 or 32): DG, DU, DU2 (the LU factors of T - s I with partial
-//    pivoting, in the layout of LAPACK's dgtsv) and X (the iterate), each 2n
-//    entries.  The factorization streams the current row in registers and
-//    applies L^-1 P^T to the right-hand side as it goes; the scale of the
-//    previous iterate is folded into the next right-hand side.
-__global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a, int ls) {
-  const int lane = threadIdx.x;
+// Vector c of a set (at(v, i): entry i of vector v) made orthogonal to the
+// orthonormal vectors p0 .. c-1 and normalized, by every thread of the block
+// (32 or 64): the dots one thread per earlier vector (four partial sums), the
+// update and the norm spread over the entries; classical Gram-Schmidt applied
+// twice, which keeps orthogonality to rounding.  Called by all threads alike.
+template <class At>
+__device__ void block_cgs2(At at, int p0, int c, int len, double* s_dot, double* s_red) {
+  const int t = threadIdx.x, T = blockDim.x;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (t >= p0 && t < c) {
+      double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+      int i = 0;
+      for (; i + 4 <= len; i += 4) {
+        d0 = fma(at(t, i), at(c, i), d0);
+        d1 = fma(at(t, i + 1), at(c, i + 1), d1);
+        d2 = fma(at(t, i + 2), at(c, i + 2), d2);
+        d3 = fma(at(t, i + 3), at(c, i + 3), d3);
+      }
+      for (; i < len; ++i) d0 = fma(at(t, i), at(c, i), d0);
+      s_dot[t] = (d0 + d1) + (d2 + d3);
+    }
+    __syncthreads();
+    for (int i = t; i < len; i += T) {
+      double x = at(c, i);
+      for (int p = p0; p < c; ++p) x = fma(-s_dot[p], at(p, i), x);
+      at(c, i) = x;
+    }
+    __syncthreads();
+  }
+  double s2 = 0.0;
+  for (int i = t; i < len; i += T) s2 = fma(at(c, i), at(c, i), s2);
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  if ((t & 31) == 0) s_red[t >> 5] = s2;
+  __syncthreads();
+  double tot = 0.0;
+  for (int w = 0; w < (T >> 5); ++w) tot += s_red[w];
+  const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
+  for (int i = t; i < len; i += T) at(c, i) *= inv;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// 3. Inverse iteration, one CTA of one or two warps per matrix (persistent
+//    over matrices), thread a for the a-th kept index.  Scratch per CTA slot,
+//    interleaved by thread with stride ls (16, 32 or 64): DG, DU, DU2 (the LU
+//    factors of T - s I with partial pivoting, in the layout of LAPACK's dgtsv)
+//    and X (the iterate), each 2n entries.  The factorization streams the
+//    current row in registers and applies L^-1 P^T to the right-hand side as
+//    it goes; the scale of the previous iterate is folded into the next
+//    right-hand side.
+__global__ void __launch_bounds__(64) k_bd_invit(BdVecArgs a, int ls) {
+  __shared__ double s_dot[kKeptMax];
+  __shared__ double s_red[2];
+  const int lane = threadIdx.x;             // kept index of this thread
+  const int wl = threadIdx.x & 31;          // lane within its warp
   double* scr = a.scratch + (size_t)blockIdx.x * 4 * (2 * a.n) * ls;   // a slot for the largest n
 #define DG(i) scr[((size_t)0 * m + (i)) * ls + lane]
 #define DU(i) scr[((size_t)1 * m + (i)) * ls + lane]
@@ -609,15 +748,16 @@ __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a, int ls) {
       n = t.n; nk = t.nk[0]; kept = t.kept; sg = t.sig; bd = t.bd; vout = t.vrows;
     } else {
       nk = a.nk[s];
-      kept = a.kept + (size_t)s * 32;
+      kept = a.kept + (size_t)s * a.kstride;
       sg = a.sig + (size_t)s * a.n_pad;
       bd = a.bd + (size_t)s * 3 * n;
-      vout = a.vrows + (size_t)s * 32 * n;
+      vout = a.vrows + (size_t)s * a.kstride * n;
     }
     const int m = 2 * n;
     // |T| (max |o_k|): T and s are scaled by 1/|T|, the pivot floor is eps
+    // (each warp reduces over all of T)
     double tn = 0.0;
-    for (int i = lane; i < n; i += 32) tn = fmax(tn, fmax(fabs(bd[i]), fabs(bd[n + i])));
+    for (int i = wl; i < n; i += 32) tn = fmax(tn, fmax(fabs(bd[i]), fabs(bd[n + i])));
     for (int o = 16; o > 0; o >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
     const double its = tn > 0.0 ? 1.0 / tn : 0.0;
     const bool on = lane < nk && lane < ls;
@@ -709,26 +849,15 @@ __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a, int ls) {
           rs = 1.0;
         }
       }
-      // Gram-Schmidt against the earlier kept vectors of the same cluster
-      // (a chain of kept values less than 1e-3 |T| apart), in lane order
+      // orthonormalize against the earlier kept vectors of the same cluster
+      // (a chain of kept values less than 1e-3 |T| apart), in index order
+      __syncthreads();
       for (int c = 1; c < nk && c < ls; ++c) {
-        __syncwarp();
         if (sg[kept[c - 1]] - sg[kept[c]] > 1e-3 * tn) continue;
-        if (lane == c) {
-          int p0 = c - 1;
-          while (p0 > 0 && sg[kept[p0 - 1]] - sg[kept[p0]] <= 1e-3 * tn) --p0;
-          for (int p = p0; p < c; ++p) {
-            double dot = 0.0;
-            for (int i = 0; i < m; ++i) dot = fma(XL(p, i), XB(i), dot);
-            for (int i = 0; i < m; ++i) XB(i) = fma(-dot, XL(p, i), XB(i));
-          }
-          double s2 = 0.0;
-          for (int i = 0; i < m; ++i) s2 = fma(XB(i), XB(i), s2);
-          const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
-          for (int i = 0; i < m; ++i) XB(i) *= inv;
-        }
+        int p0 = c - 1;
+        while (p0 > 0 && sg[kept[p0 - 1]] - sg[kept[p0]] <= 1e-3 * tn) --p0;
+        block_cgs2([&](int v, int i) -> double& { return XL(v, i); }, p0, c, m, s_dot, s_red);
       }
-      __syncwarp();
     }
 #undef OFFD
     if (on) {                                        // v_B = even entries, normalized
@@ -739,28 +868,14 @@ __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a, int ls) {
     }
     // orthogonal z's of a cluster need not have orthogonal halves (values near
     // the noise level mix +s and -s): orthonormalize the v's of each cluster too
+    __syncthreads();
     for (int c = 1; c < nk && c < ls; ++c) {
-      __syncwarp();
       if (sg[kept[c - 1]] - sg[kept[c]] > 1e-3 * tn) continue;
-      if (lane == c) {
-        int p0 = c - 1;
-        while (p0 > 0 && sg[kept[p0 - 1]] - sg[kept[p0]] <= 1e-3 * tn) --p0;
-        double* vc = vout + (size_t)c * n;
-        for (int pass = 0; pass < 2; ++pass) {       // twice: classical Gram-Schmidt loses orthogonality once
-          for (int p = p0; p < c; ++p) {
-            const double* vp = vout + (size_t)p * n;
-            double dot = 0.0;
-            for (int i = 0; i < n; ++i) dot = fma(vp[i], vc[i], dot);
-            for (int i = 0; i < n; ++i) vc[i] = fma(-dot, vp[i], vc[i]);
-          }
-        }
-        double s2 = 0.0;
-        for (int i = 0; i < n; ++i) s2 = fma(vc[i], vc[i], s2);
-        const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
-        for (int i = 0; i < n; ++i) vc[i] *= inv;
-      }
+      int p0 = c - 1;
+      while (p0 > 0 && sg[kept[p0 - 1]] - sg[kept[p0]] <= 1e-3 * tn) --p0;
+      block_cgs2([&](int v, int i) -> double& { return vout[(size_t)v * n + i]; }, p0, c, n, s_dot, s_red);
     }
-    __syncwarp();
+    __syncthreads();
   }
 #undef DG
 #undef DU
@@ -770,14 +885,14 @@ __global__ void __launch_bounds__(32) k_bd_invit(BdVecArgs a, int ls) {
 }
 
 // ---------------------------------------------------------------------------
-// 4. v = H_0 H_1 ... H_{n-3} v_B, one CTA of 4 warps per (matrix, group of 16
-//    kept vectors), the group in shared memory, 4 vectors per warp (warps
+// 4. v = H_0 H_1 ... H_{n-3} v_B, one CTA of gs / 4 warps per (matrix, group
+//    of gs kept vectors; gs = 16, or 8 for sides whose 16 vectors would not fit
+//    in shared memory), the group in shared memory, 4 vectors per warp (warps
 //    independent: no block barrier inside the reflector loop).  The four dot
 //    products of a warp are reduced together (reduce4).
-constexpr int kBtGroup = 16;
-__global__ void __launch_bounds__(128) k_bd_backtr(BdVecArgs a) {
-  extern __shared__ double V[];                      // [kBtGroup][n]
-  const int s = blockIdx.x, g0 = blockIdx.y * kBtGroup;
+__global__ void __launch_bounds__(128) k_bd_backtr(BdVecArgs a, int gs) {
+  extern __shared__ double V[];                      // [gs][n]
+  const int s = blockIdx.x, g0 = blockIdx.y * gs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int n = a.n, nk_all;
   double* vrow;
@@ -791,13 +906,13 @@ __global__ void __launch_bounds__(128) k_bd_backtr(BdVecArgs a) {
     kept = t.kept + g0; sg = t.sig;
   } else {
     nk_all = a.nk[s];
-    vrow = a.vrows + ((size_t)s * 32 + g0) * n;
+    vrow = a.vrows + ((size_t)s * a.kstride + g0) * n;
     R = a.R + (size_t)s * n * n;
     tauR = a.bd + (size_t)s * 3 * n + 2 * n;
-    kept = a.kept + (size_t)s * 32 + g0;
+    kept = a.kept + (size_t)s * a.kstride + g0;
     sg = a.sig + (size_t)s * a.n_pad;
   }
-  const int nk = min(nk_all - g0, kBtGroup);         // vectors of this group
+  const int nk = min(nk_all - g0, gs);               // vectors of this group
   if (nk <= 0) return;
   for (int e = threadIdx.x; e < nk * n; e += blockDim.x) V[e] = vrow[e];
   __syncthreads();
@@ -837,21 +952,10 @@ __global__ void __launch_bounds__(128) k_bd_backtr(BdVecArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-template <int NQ>
-static cudaError_t launch_bidiag_nq(const BidiagArgs& a, cudaStream_t st) {
-  const int n = a.n;
-  const size_t rows = (size_t)n * n * sizeof(double);
-  const size_t aux = ((size_t)(3 + kBdThreads / 32) * n + 32) * sizeof(double);
-  const int use_smem = rows + aux <= 200 * 1024;
-  // rows in the global workspace: ask for enough shared memory that one CTA
-  // runs per SM, so the resident matrices stay in L2
-  const size_t smem = use_smem ? rows + aux : std::max<size_t>(aux, 120 * 1024);
-  static std::atomic<uint64_t> attr{0};
-  cudaError_t e = raise_smem_limit(k_bidiag<NQ>, 200 * 1024 + 1024, attr);
-  if (e != cudaSuccess) return e;
-  k_bidiag<NQ><<<a.S, kBdThreads, smem, st>>>(a, use_smem);
-  return cudaGetLastError();
-}
+// Largest side of the bidiagonalization route: the wide form's per-step
+// vectors (3 + 8 per-warp rows of n doubles) fill shared memory at 2304.
+constexpr int kBdMaxN = 2304;
+constexpr size_t kBdSmemCap = 227 * 1024;
 
 // Dynamic shared memory of a launch over matrices of side n (the working copy
 // in shared memory when it fits, else the per-step vectors with enough
@@ -863,9 +967,23 @@ size_t bidiag_smem_bytes(int n) {
 }
 
 template <int NQ>
+static cudaError_t launch_bidiag_nq(const BidiagArgs& a, cudaStream_t st) {
+  const int n = a.n;
+  const int use_smem = NQ > 0 && (size_t)n * n * sizeof(double) +
+                                         ((size_t)(3 + kBdThreads / 32) * n + 32) * sizeof(double) <=
+                                     200 * 1024;
+  const size_t smem = bidiag_smem_bytes(n);
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t e = raise_smem_limit(k_bidiag<NQ>, kBdSmemCap, attr);
+  if (e != cudaSuccess) return e;
+  k_bidiag<NQ><<<a.S, kBdThreads, smem, st>>>(a, use_smem);
+  return cudaGetLastError();
+}
+
+template <int NQ>
 static cudaError_t launch_bidiag_items_nq(const SvdItem* items, int S, size_t smem, cudaStream_t st) {
   static std::atomic<uint64_t> attr{0};
-  cudaError_t e = raise_smem_limit(k_bidiag<NQ>, 200 * 1024 + 1024, attr);
+  cudaError_t e = raise_smem_limit(k_bidiag<NQ>, kBdSmemCap, attr);
   if (e != cudaSuccess) return e;
   BidiagArgs a{};
   a.S = S; a.items = items;
@@ -875,13 +993,14 @@ static cudaError_t launch_bidiag_items_nq(const SvdItem* items, int S, size_t sm
 
 cudaError_t launch_bidiag_items(const SvdItem* items, int S, int n_max, size_t smem, cudaStream_t st) {
   if (S <= 0) return cudaSuccess;
-  if (smem > 200 * 1024 + 1024) return cudaErrorInvalidValue;
+  if (smem > kBdSmemCap || smem < bidiag_smem_bytes(n_max)) return cudaErrorInvalidValue;
   if (n_max <= 64) return launch_bidiag_items_nq<2>(items, S, smem, st);
   if (n_max <= 128) return launch_bidiag_items_nq<4>(items, S, smem, st);
   if (n_max <= 256) return launch_bidiag_items_nq<8>(items, S, smem, st);
   if (n_max <= 512) return launch_bidiag_items_nq<16>(items, S, smem, st);
   if (n_max <= 768) return launch_bidiag_items_nq<24>(items, S, smem, st);
   if (n_max <= 1024) return launch_bidiag_items_nq<32>(items, S, smem, st);
+  if (n_max <= kBdMaxN) return launch_bidiag_items_nq<0>(items, S, smem, st);
   return cudaErrorInvalidValue;
 }
 
@@ -893,6 +1012,7 @@ cudaError_t launch_bidiag(const BidiagArgs& a, cudaStream_t st) {
   if (a.n <= 512) return launch_bidiag_nq<16>(a, st);
   if (a.n <= 768) return launch_bidiag_nq<24>(a, st);
   if (a.n <= 1024) return launch_bidiag_nq<32>(a, st);
+  if (a.n <= kBdMaxN) return launch_bidiag_nq<0>(a, st);
   return cudaErrorInvalidValue;
 }
 
@@ -919,33 +1039,40 @@ cudaError_t launch_bd_bisect_items(const SvdItem* items, int S, int n_max, cudaS
   return cudaGetLastError();
 }
 
-// Warp slots of the inverse iteration: up to eight per SM (each runs one
-// lane-serial chain per kept vector, so the SMs need several to hide the FP64
-// latency), and no more than 512 MB of scratch (4 x 2n x 32 doubles each).
-static int invit_slots(int n, int S) {
-  const size_t per = (size_t)4 * 2 * n * 32 * sizeof(double);
+// Thread stride of the inverse iteration's scratch: 16, 32 or 64 kept vectors.
+static int invit_stride(int kmax) { return kmax <= 16 ? 16 : (kmax <= 32 ? 32 : 64); }
+
+// CTA slots of the inverse iteration: up to eight per SM (each runs one
+// thread-serial chain per kept vector, so the SMs need several to hide the
+// FP64 latency), and no more than 512 MB of scratch (4 x 2n x ls doubles each).
+static int invit_slots(int n, int S, int kmax) {
+  const size_t per = (size_t)4 * 2 * n * invit_stride(kmax) * sizeof(double);
   const int by_mem = (int)std::max<size_t>(152, ((size_t)512 << 20) / per);
   return std::max(1, std::min(S, std::min(152 * 8, by_mem)));
 }
 
-// Scratch of the inverse iteration (the lane stride used is 16 when at most 16
-// vectors are kept, 32 otherwise).
-size_t bd_vectors_scratch_doubles(int n, int S) { return (size_t)invit_slots(n, S) * 4 * 2 * n * 32; }
+size_t bd_vectors_scratch_doubles(int n, int S, int kmax) {
+  return (size_t)invit_slots(n, S, kmax) * 4 * 2 * n * invit_stride(kmax);
+}
 
 // Ragged: a.items holds a.S matrices, a.n the largest side, a.kmax the largest
-// kept count, a.scratch bd_vectors_scratch_doubles(a.n, a.S) doubles.
+// kept count, a.scratch bd_vectors_scratch_doubles(a.n, a.S, a.kmax) doubles.
 cudaError_t launch_bd_vectors(const BdVecArgs& a, cudaStream_t st) {
   if (a.S <= 0) return cudaSuccess;
-  const size_t smem = (size_t)kBtGroup * a.n * sizeof(double);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  k_bd_invit<<<invit_slots(a.n, a.S), 32, 0, st>>>(a, a.kmax <= 16 ? 16 : 32);
+  if (a.kmax > kKeptMax || (!a.items && a.kstride < a.kmax)) return cudaErrorInvalidValue;
+  constexpr size_t kSmemCap = 227 * 1024;
+  const int gs = (size_t)16 * a.n * sizeof(double) <= kSmemCap ? 16 : 8;
+  const size_t smem = (size_t)gs * a.n * sizeof(double);
+  if (smem > kSmemCap) return cudaErrorInvalidValue;
+  const int ls = invit_stride(a.kmax);
+  k_bd_invit<<<invit_slots(a.n, a.S, a.kmax), ls > 32 ? 64 : 32, 0, st>>>(a, ls);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   static std::atomic<uint64_t> attr{0};
-  e = raise_smem_limit(k_bd_backtr, 200 * 1024, attr);
+  e = raise_smem_limit(k_bd_backtr, kSmemCap, attr);
   if (e != cudaSuccess) return e;
-  const dim3 grid((unsigned)a.S, (unsigned)((std::max(1, a.kmax) + kBtGroup - 1) / kBtGroup));
-  k_bd_backtr<<<grid, 128, smem, st>>>(a);
+  const dim3 grid((unsigned)a.S, (unsigned)((std::max(1, a.kmax) + gs - 1) / gs));
+  k_bd_backtr<<<grid, 32 * (gs / 4), smem, st>>>(a, gs);
   return cudaGetLastError();
 }
 

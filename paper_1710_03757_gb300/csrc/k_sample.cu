@@ -21,27 +21,31 @@
 //
 // One CTA of 128 threads per item (trajectory, tensor): warp 0 builds E while
 // warp 1 builds G (the row recurrences run along i with one lane per column,
-// neighbouring columns exchanged by warp shuffles); warp 0 then draws with a
-// ballot search per step and computes the chi rates; all warps write halves
+// and a second column per lane past 32, neighbouring columns exchanged by warp
+// shuffles); warp 0 then draws with a ballot search per step and computes the
+// chi rates; all warps write halves
 //   left[row][a]  = sqrt(s~_a) u_a[row],   right[a][col] = sqrt(s~_a) v_a[col],
 // s~ = (s / s_1) / r, u = M v / s computed here for the kept indices only.
 #include <cmath>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
+#include "kernels_bd.h"
 
 namespace mctrg {
 
 namespace {
 constexpr int kThreads = 128;
-constexpr int kVch = 16;    // kept vectors staged per pass of the M v product
 
-// Sum of 16 per-lane values over the warp, all at once: four halving exchanges
-// (each lane keeps the half of its values its partner does not) and a last
-// butterfly; on return lane l holds the total of value (l >> 1).
-__device__ __forceinline__ double warp_sum16(double (&v)[16], int lane) {
+// Sum of KV (16 or 8) per-lane values over the warp, all at once: halving
+// exchanges (each lane keeps the half of its values its partner does not) and
+// last butterflies; on return lane l holds the total of value l / (32 / KV).
+template <int KV>
+__device__ __forceinline__ double warp_sum_k(double (&v)[KV], int lane) {
 #pragma unroll
-  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+  for (int h = KV / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
     const bool hi = lane & o;
 #pragma unroll
     for (int j = 0; j < h; ++j) {
@@ -50,7 +54,10 @@ __device__ __forceinline__ double warp_sum16(double (&v)[16], int lane) {
       v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+  double t = v[0];
+#pragma unroll
+  for (int o = 16 / KV; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -63,15 +70,24 @@ size_t sample_scratch_doubles(int n, int chi, int grid) {
   return (size_t)grid * (size_t)(n + 1) * (size_t)(2 * chi + 1);
 }
 
+int sample_grid(int n, int chi) {
+  const size_t per = sample_scratch_doubles(n, chi, 1) * sizeof(double);
+  const size_t cap = ((size_t)256 << 20) / per;
+  return (int)std::max<size_t>(152, std::min<size_t>(1024, cap));
+}
+
+// KV kept vectors are staged per pass of the M v product (16, or 8 for sides
+// whose 16 staged rows would not fit in shared memory).
+template <int KV>
 __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
   extern __shared__ double dsm[];
-  const int n = a.n, np = a.n_pad, chi = a.chi, kc = a.kc;
+  const int n = a.n, np = a.n_pad, chi = a.chi, kc = a.kc, ks = a.kstride;
   double* w = dsm;                                  // [np] normalized weights
   double* wn = w + np;                              // [np] s_i / s_1
-  double* vbuf = wn + np;                           // [kVch][n]
-  unsigned char* inset = (unsigned char*)(vbuf + (size_t)kVch * n);   // [np]
-  __shared__ int s_kept[32];
-  __shared__ double s_sigt[32];
+  double* vbuf = wn + np;                           // [KV][n]
+  unsigned char* inset = (unsigned char*)(vbuf + (size_t)KV * n);   // [np]
+  __shared__ int s_kept[kKeptMax];
+  __shared__ double s_sigt[kKeptMax];
   __shared__ int s_nk;
   __shared__ uint32_t s_flags;
 
@@ -90,7 +106,7 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
     const bool sample = a.stochastic && nz > chi;
 
     if (a.mode == 2) {                         // choices made earlier (split form)
-      if (tid < 32) { s_kept[tid] = a.kept[it * 32 + tid]; s_sigt[tid] = a.sigt[it * 32 + tid]; }
+      if (tid < ks) { s_kept[tid] = a.kept[it * ks + tid]; s_sigt[tid] = a.sigt[it * ks + tid]; }
       if (tid == 0) { s_nk = a.nk[it]; s_flags = 0; }
       __syncthreads();
     } else {
@@ -106,36 +122,59 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
     __syncthreads();
 
     if (sample) {
-      if (warp == 0) {                       // forward table E, lane l <-> column l+1
-        const int j = lane + 1;
+      const bool two = chi > 32;             // a second column per lane (32 + lane + 1)
+      if (warp == 0) {                       // forward table E, lane l <-> columns l+1, l+33
+        const int j = lane + 1, j2 = lane + 33;
         const double wj = (j <= chi) ? w[j - 1] : 1.0;
-        double Ej = 0.0;
+        const double wj2 = (j2 <= chi) ? w[j2 - 1] : 1.0;
+        double Ej = 0.0, Ej2 = 0.0;
         if (lane == 0) tabE[0] = 1.0;
         if (j <= chi) tabE[j] = 0.0;
+        if (j2 <= chi) tabE[j2] = 0.0;
         for (int i = 1; i <= nz; ++i) {
           const double wi = w[i - 1];
           double prev = __shfl_up_sync(0xffffffffu, Ej, 1);
           if (lane == 0) prev = 1.0;
-          Ej = Ej + (wi / wj) * prev;
           double* row = tabE + (size_t)i * (chi + 1);
+          if (two) {                         // column 33's left neighbour is lane 31's column 32
+            const double top = __shfl_sync(0xffffffffu, Ej, 31);
+            double prev2 = __shfl_up_sync(0xffffffffu, Ej2, 1);
+            if (lane == 0) prev2 = top;
+            Ej2 = Ej2 + (wi / wj2) * prev2;
+            if (j2 <= chi) row[j2] = Ej2;
+          }
+          Ej = Ej + (wi / wj) * prev;
           if (lane == 0) row[0] = 1.0;
           if (j <= chi) row[j] = Ej;
         }
-      } else if (warp == 1) {                // backward table G, lane l <-> column l+1
-        const int bb = lane + 1;
-        double Gb = 0.0;
+      } else if (warp == 1) {                // backward table G, lane l <-> columns l+1, l+33
+        const int bb = lane + 1, bb2 = lane + 33;
+        double Gb = 0.0, Gb2 = 0.0;
         if (lane == 0) tabG[(size_t)nz * chi] = 1.0;
         if (bb < chi) tabG[(size_t)nz * chi + bb] = 0.0;
+        if (bb2 < chi) tabG[(size_t)nz * chi + bb2] = 0.0;
         for (int i = nz - 1; i >= 0; --i) {
           double prev = __shfl_up_sync(0xffffffffu, Gb, 1);
           if (lane == 0) prev = 1.0;
+          double* row = tabG + (size_t)i * chi;
+          if (two) {
+            const double top = __shfl_sync(0xffffffffu, Gb, 31);
+            double prev2 = __shfl_up_sync(0xffffffffu, Gb2, 1);
+            if (lane == 0) prev2 = top;
+            if (bb2 <= nz - i) {
+              const double first = (i + bb2 + 1 <= nz) ? Gb2 * (w[i + bb2] / w[i]) : 0.0;
+              Gb2 = first + prev2;
+            } else {
+              Gb2 = 0.0;
+            }
+            if (bb2 < chi) row[bb2] = Gb2;
+          }
           if (bb <= nz - i) {
             const double first = (i + bb + 1 <= nz) ? Gb * (w[i + bb] / w[i]) : 0.0;
             Gb = first + prev;
           } else {
             Gb = 0.0;
           }
-          double* row = tabG + (size_t)i * chi;
           if (lane == 0) row[0] = 1.0;
           if (bb < chi) row[bb] = Gb;
         }
@@ -165,9 +204,9 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
           bcur = found - 1;
         }
         __syncwarp();
-        // inclusion rate of each kept index (lane a <-> a-th pick)
-        if (lane < chi) {
-          const int I = s_kept[lane] + 1;                       // 1-based
+        // inclusion rate of each kept index (lane a <-> picks a and a + 32)
+        for (int pk = lane; pk < chi; pk += 32) {
+          const int I = s_kept[pk] + 1;                         // 1-based
           const int alo = max(0, chi - 1 - (nz - I)), ahi = min(chi - 1, I - 1);
           double R = 1.0;
           for (int q = 0; q < chi - ahi; ++q) R *= w[I - 1 + q] / w[ahi + q];
@@ -177,16 +216,21 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
             if (aa > alo) R *= w[I + chi - aa - 1] / w[aa - 1];
           }
           const double r = acc / tabE[(size_t)nz * (chi + 1) + chi];
-          s_sigt[lane] = wn[I - 1] / r;
+          s_sigt[pk] = wn[I - 1] / r;
         }
         __syncwarp();
         // ascending order of the kept indices (distinct, so ranks are unique)
-        int mine = lane < chi ? s_kept[lane] : 0;
-        double mys = lane < chi ? s_sigt[lane] : 0.0;
-        int rank = 0;
-        for (int q = 0; q < chi; ++q) rank += s_kept[q] < mine;
+        const int pk2 = lane + 32;
+        const int mine = lane < chi ? s_kept[lane] : 0, mine2 = pk2 < chi ? s_kept[pk2] : 0;
+        const double mys = lane < chi ? s_sigt[lane] : 0.0, mys2 = pk2 < chi ? s_sigt[pk2] : 0.0;
+        int rank = 0, rank2 = 0;
+        for (int q = 0; q < chi; ++q) {
+          rank += s_kept[q] < mine;
+          rank2 += s_kept[q] < mine2;
+        }
         __syncwarp();
         if (lane < chi) { s_kept[rank] = mine; s_sigt[rank] = mys; inset[mine] = 1; }
+        if (pk2 < chi) { s_kept[rank2] = mine2; s_sigt[rank2] = mys2; inset[mine2] = 1; }
         if (lane == 0 && fl) atomicOr(&s_flags, fl);
       }
     } else {
@@ -206,9 +250,9 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
     }
     if (a.mode == 1) {                         // split form: hand the choices on
       __syncthreads();
-      if (tid < 32) {
-        a.kept[it * 32 + tid] = tid < nk0 ? s_kept[tid] : 0;
-        a.sigt[it * 32 + tid] = tid < nk0 ? s_sigt[tid] : 0.0;
+      if (tid < ks) {
+        a.kept[it * ks + tid] = tid < nk0 ? s_kept[tid] : 0;
+        a.sigt[it * ks + tid] = tid < nk0 ? s_sigt[tid] : 0.0;
       }
       if (tid == 0) {
         a.nk[it] = nk0;
@@ -230,7 +274,7 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
       double v = 0.0;
       if (al < nk) {
         const int r = s_kept[al];
-        const double* brow = a.mode == 2 ? a.vrows + ((size_t)it * 32 + al) * n : Wm + (size_t)pm[r] * n;
+        const double* brow = a.mode == 2 ? a.vrows + ((size_t)it * ks + al) * n : Wm + (size_t)pm[r] * n;
         v = sqrt(s_sigt[al]) * brow[col] / sg[r];
       }
       Hr[idx] = v;
@@ -249,29 +293,29 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
         const int al = idx - (idx / kc) * kc;
         if (al >= nk) Hl[idx] = 0.0;
       }
-      for (int a0 = 0; a0 < nk; a0 += kVch) {
-        const int nv = min(kVch, nk - a0);
+      for (int a0 = 0; a0 < nk; a0 += KV) {
+        const int nv = min(KV, nk - a0);
         __syncthreads();
         for (int idx = tid; idx < nv * n; idx += kThreads) {
           const int q = idx / n, col = idx - q * n;
-          vbuf[idx] = a.mode == 2 ? a.vrows[((size_t)it * 32 + a0 + q) * n + col]
+          vbuf[idx] = a.mode == 2 ? a.vrows[((size_t)it * ks + a0 + q) * n + col]
                                   : Wm[(size_t)pm[s_kept[a0 + q]] * n + col];
         }
         __syncthreads();
         for (int row = warp; row < n; row += kThreads / 32) {
-          double acc[kVch];
+          double acc[KV];
 #pragma unroll
-          for (int q = 0; q < kVch; ++q) acc[q] = 0.0;
+          for (int q = 0; q < KV; ++q) acc[q] = 0.0;
           const double* mr = Mm + (size_t)row * n;
           for (int col = lane; col < n; col += 32) {
             const double mv = mr[col];
 #pragma unroll
-            for (int q = 0; q < kVch; ++q)
+            for (int q = 0; q < KV; ++q)
               if (q < nv) acc[q] = fma(mv, vbuf[q * n + col], acc[q]);
           }
-          const double sum = warp_sum16(acc, lane);
-          const int q = lane >> 1;
-          if (!(lane & 1) && q < nv) {
+          const double sum = warp_sum_k<KV>(acc, lane);
+          const int q = lane / (32 / KV);
+          if (lane % (32 / KV) == 0 && q < nv) {
             const int r = s_kept[a0 + q];
             const double sr = sg[r];
             Hl[(size_t)row * kc + a0 + q] = sqrt(s_sigt[a0 + q]) * sum / (sr * sr);
@@ -287,14 +331,25 @@ __global__ void __launch_bounds__(kThreads) k_sample_split(SampleArgs a) {
 
 cudaError_t launch_sample_split(const SampleArgs& a, cudaStream_t st, int grid) {
   if (a.n_items <= 0) return cudaSuccess;
-  if (a.chi > 32 || a.kc > 32) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)a.n_pad * 2 * sizeof(double) + (size_t)kVch * a.n * sizeof(double) +
-                      (size_t)a.n_pad + 16;
-  static std::atomic<uint64_t> attr{0};
-  cudaError_t e = raise_smem_limit(k_sample_split, 160 * 1024, attr);
-  if (e != cudaSuccess) return e;
+  if (a.chi > kKeptMax || a.kc > kKeptMax || (a.mode != 0 && a.kstride < std::max(a.chi, a.kc)))
+    return cudaErrorInvalidValue;
+  const auto smem_for = [&](int kv) {
+    return (size_t)a.n_pad * 2 * sizeof(double) + (size_t)kv * a.n * sizeof(double) + (size_t)a.n_pad + 16;
+  };
   if (grid > a.n_items) grid = (int)a.n_items;
-  k_sample_split<<<grid, kThreads, smem, st>>>(a);
+  constexpr size_t kSmemCap = 227 * 1024;
+  if (smem_for(16) <= 160 * 1024) {
+    static std::atomic<uint64_t> attr{0};
+    cudaError_t e = raise_smem_limit(k_sample_split<16>, kSmemCap, attr);
+    if (e != cudaSuccess) return e;
+    k_sample_split<16><<<grid, kThreads, smem_for(16), st>>>(a);
+  } else {
+    if (smem_for(8) > kSmemCap) return cudaErrorInvalidValue;
+    static std::atomic<uint64_t> attr{0};
+    cudaError_t e = raise_smem_limit(k_sample_split<8>, kSmemCap, attr);
+    if (e != cudaSuccess) return e;
+    k_sample_split<8><<<grid, kThreads, smem_for(8), st>>>(a);
+  }
   return cudaGetLastError();
 }
 

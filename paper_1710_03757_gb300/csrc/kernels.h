@@ -52,18 +52,24 @@ struct SampleArgs {
   uint32_t* iflags;     // [items] |= truncation flags (indexed item - h_item0); may be null
   double* scratch;      // tables: gridDim * (n + 1) * (2 chi + 1) doubles
   // Split form (bidiagonalization route, whose vectors exist only for the kept
-  // indices): mode 1 chooses and writes kept[it][32] (ranks, ascending),
-  // sigt[it][32] (reweighted values s~) and nk[it], without halves; mode 2
+  // indices): mode 1 chooses and writes kept[it][kstride] (ranks, ascending),
+  // sigt[it][kstride] (reweighted values s~) and nk[it], without halves; mode 2
   // reads them back and writes the halves from vrows[it][a][col] = s_r v_r[col]
   // (r = kept[it][a]) instead of W / perm.  it = item - item0.  mode 0: both.
+  // kstride = kept_stride(chi) (32, or 64 above 32 kept values).
   int mode;
   int* kept;
   double* sigt;
   int* nk;
   const double* vrows;
+  int kstride;
 };
+// chi and kc at most 64 (kKeptMax).
 cudaError_t launch_sample_split(const SampleArgs& a, cudaStream_t st, int grid);
 size_t sample_scratch_doubles(int n, int chi, int grid);
+// CTAs of a sampler launch over n x n spectra: up to 1024, fewer when the
+// tables of that many would pass 256 MB (at least 152, one per SM).
+int sample_grid(int n, int chi);
 
 // Shared mode helper: unit left vectors u_r = M v_r / s_r for r < nnz by rank.
 cudaError_t launch_u_rows(const double* M, const double* W, const double* sig, const int* perm,

@@ -5,6 +5,11 @@
 
 namespace mctrg {
 
+// Stride of the per-matrix kept-index arrays (kept ranks, reweighted values,
+// kept vectors) for a kept count kc <= 64: 32 up to 32 kept values, else 64.
+inline int kept_stride(int kc) { return kc <= 32 ? 32 : 64; }
+constexpr int kKeptMax = 64;
+
 // One matrix of a ragged launch: matrices of different sizes (and owners) in
 // one launch of the bidiagonalization route, each with its own buffers.
 struct SvdItem {
@@ -15,9 +20,9 @@ struct SvdItem {
   int* perm;          // n_pad
   int* nnz;           // 1
   double* lns1;       // 1 (may be null)
-  const int* kept;    // 32 kept ranks (ascending)
+  const int* kept;    // kept ranks (ascending), up to 64
   const int* nk;      // 1
-  double* vrows;      // 32 x n: s_r v_r of the kept ranks
+  double* vrows;      // nk x n: s_r v_r of the kept ranks
   double zero_rel;    // zero threshold (<= 0: n 2^-52)
   int n, n_pad;
 };
@@ -26,6 +31,8 @@ struct SvdItem {
 //    row-major n x n matrices.  bd[s] = [d (n) | e (n, e[n-1] = 0) | tauR (n)];
 //    the right reflector of step k, u_k = (1, R[k][k+2], ..., R[k][n-1]) on
 //    columns k+1.., stays in row k of the working copy R = W[s] (n x n).
+//    Sides up to 1024 keep a row's columns in registers; larger sides (up to
+//    2304) stream them in two passes per row group.
 struct BidiagArgs {
   const double* M;   // [S][n][n] read only
   double* W;         // [S][n][n] (any row stride >= n is not supported: n x n)
@@ -54,21 +61,22 @@ cudaError_t launch_bd_bisect_items(const SvdItem* items, int S, int n_max, cudaS
 //    receives s_r v_r for r = kept[s][a] (the scaling of a Jacobi row),
 //    computed by inverse iteration on the Golub-Kahan tridiagonal
 //    (reorthogonalized within clusters of close kept values) and the right
-//    reflectors.  scratch: bd_vectors_scratch_doubles(n, S) doubles.
+//    reflectors.  scratch: bd_vectors_scratch_doubles(n, S, kmax) doubles.
 struct BdVecArgs {
   const double* bd;     // [S][3n]
   const double* R;      // [S][n][n] reflectors (row k holds u_k)
   const double* sig;    // [S][n_pad]
-  const int* kept;      // [S][32]
+  const int* kept;      // [S][kstride]
   const int* nk;        // [S]
-  double* vrows;        // [S][32][n]
+  double* vrows;        // [S][kstride][n]
   double* scratch;
   int n, n_pad, S;
   int unit_rows;        // 1: write v_r itself instead of s_r v_r
-  int kmax;             // largest nk of the batch (<= 32)
+  int kmax;             // largest nk of the batch (<= 64)
+  int kstride;          // kept_stride of the largest kept count (non-ragged layout)
   const SvdItem* items = nullptr;   // ragged: S matrices described here (n = the largest)
 };
 cudaError_t launch_bd_vectors(const BdVecArgs& a, cudaStream_t st);
-size_t bd_vectors_scratch_doubles(int n, int S);
+size_t bd_vectors_scratch_doubles(int n, int S, int kmax);
 
 }  // namespace mctrg

@@ -302,7 +302,8 @@ int mctrg_ctx::init_from_device_tensor(int D0, int L_, int chi_) {
 // SVD route of a level whose n x n matrices are X Yt^T with inner dimension K.
 namespace mctrg {
 bool route_bidiag(const mctrg_options& o, int n, int K) {
-  if (o.svd == MCTRG_SVD_JACOBI || n > 1024) return false;
+  if (n > 1024) return true;            // beyond the Jacobi kernels' layouts, whatever the option
+  if (o.svd == MCTRG_SVD_JACOBI) return false;
   if (o.svd == MCTRG_SVD_BIDIAG) return n >= 2;
   return n >= 64 && 2 * K >= n;
 }
@@ -314,7 +315,7 @@ static bool is_pow2(int L) { return L >= 2 && (L & (L - 1)) == 0; }
 
 extern "C" int mctrg_init_lattice(mctrg_ctx_t c, double beta, double h, int L, int chi) {
   if (!c) return MCTRG_EINVAL;
-  if (!is_pow2(L) || L > 65536 || chi < 1 || chi > 32 || !(beta >= 0.0) || !std::isfinite(beta) ||
+  if (!is_pow2(L) || L > 65536 || chi < 1 || chi > kMaxChi || !(beta >= 0.0) || !std::isfinite(beta) ||
       !std::isfinite(h))
     return MCTRG_EINVAL;
   CK(cudaSetDevice(c->opt.device));
@@ -325,7 +326,7 @@ extern "C" int mctrg_init_lattice(mctrg_ctx_t c, double beta, double h, int L, i
 
 extern "C" int mctrg_init_bond_lattice(mctrg_ctx_t c, double beta, double h, int L, int chi) {
   if (!c) return MCTRG_EINVAL;
-  if (!is_pow2(L) || L > 65536 || chi < 1 || chi > 32 || !(beta >= 0.0) || !std::isfinite(beta) ||
+  if (!is_pow2(L) || L > 65536 || chi < 1 || chi > kMaxChi || !(beta >= 0.0) || !std::isfinite(beta) ||
       !std::isfinite(h))
     return MCTRG_EINVAL;
   CK(cudaSetDevice(c->opt.device));
@@ -336,7 +337,7 @@ extern "C" int mctrg_init_bond_lattice(mctrg_ctx_t c, double beta, double h, int
 
 extern "C" int mctrg_init_impurity(mctrg_ctx_t c, double beta, double h, int L, int chi, int n_imp) {
   if (!c) return MCTRG_EINVAL;
-  if (!is_pow2(L) || L > 65536 || chi < 1 || chi > 32 || !(beta >= 0.0) || !std::isfinite(beta) ||
+  if (!is_pow2(L) || L > 65536 || chi < 1 || chi > kMaxChi || !(beta >= 0.0) || !std::isfinite(beta) ||
       !std::isfinite(h) || (n_imp != 1 && n_imp != 2) || c->opt.deterministic_levels > 0)
     return MCTRG_EINVAL;
   CK(cudaSetDevice(c->opt.device));
@@ -388,7 +389,7 @@ extern "C" int mctrg_ratio_estimate(const mctrg_estimate* num, const mctrg_estim
 
 extern "C" int mctrg_init_tensor(mctrg_ctx_t c, const double* T0, int D, int L, int chi) {
   if (!c || !T0) return MCTRG_EINVAL;
-  if (!is_pow2(L) || L > 65536 || chi < 1 || chi > 32 || D < 1 || D > 8) return MCTRG_EINVAL;
+  if (!is_pow2(L) || L > 65536 || chi < 1 || chi > kMaxChi || D < 1 || D > 8) return MCTRG_EINVAL;
   CK(cudaSetDevice(c->opt.device));
   const size_t bytes = sizeof(double) * (size_t)D * D * D * D;
   CK(c->T0.ensure(bytes));
@@ -413,6 +414,20 @@ static size_t tc_operand_bytes(int prec, int n, int d2) {
 }
 
 namespace mctrg {
+// The sampler's CTA count for a run over levels s0 .. nlev-1 (from the largest
+// side), and the table scratch it needs.
+int run_sample_grid(const std::vector<LevelInfo>& lv, int s0, int nlev, int chi) {
+  int nmax = 1;
+  for (int k = s0; k < nlev; ++k) nmax = std::max(nmax, lv[k].n);
+  return sample_grid(nmax, chi);
+}
+size_t run_sample_scratch(const std::vector<LevelInfo>& lv, int s0, int nlev, int chi) {
+  const int g = run_sample_grid(lv, s0, nlev, chi);
+  size_t m = 0;
+  for (int k = s0; k < nlev; ++k) m = std::max(m, sample_scratch_doubles(lv[k].n, chi, g));
+  return m;
+}
+
 // Memory plan of a run of n_samples trajectories over levels s0 .. nlev-1 of
 // lv (sampled; the shared prefix is held separately): B trajectories per
 // chunk, S items per sub-batch, and the device bytes the run holds.  At most
@@ -437,8 +452,9 @@ void plan_run(const std::vector<LevelInfo>& lv, int s0, int nlev, int chi, const
                   (a.n_pad + 1) * sizeof(int) + sizeof(double) + sizeof(uint32_t);
       pi += tc_operand_bytes(opt.precision, a.n, (int)d2);
       if (route_bidiag(opt, a.n, (int)d2)) {   // d, e, tau; kept values and vectors
-        pi += (3 * (size_t)a.n + 32 + 32 * (size_t)a.n) * sizeof(double) + 33 * sizeof(int);
-        bd_scr = std::max(bd_scr, bd_vectors_scratch_doubles(a.n, 1 << 16) * sizeof(double));
+        const size_t ks = kept_stride(chi);
+        pi += (3 * (size_t)a.n + ks + ks * (size_t)a.n) * sizeof(double) + (ks + 1) * sizeof(int);
+        bd_scr = std::max(bd_scr, bd_vectors_scratch_doubles(a.n, 1 << 16, a.kc) * sizeof(double));
       }
       per_item = std::max(per_item, pi);
     }
@@ -454,7 +470,7 @@ void plan_run(const std::vector<LevelInfo>& lv, int s0, int nlev, int chi, const
     per_item = std::max(per_item, ((size_t)a.n * a.n + (size_t)a.n_pad * a.n + a.n_pad) * sizeof(double) +
                                       (a.n_pad + 1) * sizeof(int) + sizeof(double) + sizeof(uint32_t));
   }
-  const size_t tables = sample_scratch_doubles(lv[nlev - 1].n, chi, 1024) * sizeof(double) + bd_scr;
+  const size_t tables = run_sample_scratch(lv, s0, nlev, chi) * sizeof(double) + bd_scr;
   const int64_t Bmax = opt.max_chunk > 0 ? std::min<int64_t>(opt.max_chunk, n_samples) : n_samples;
   const size_t work_budget = std::max<size_t>(budget / 4, 1);
   S = per_item ? (int64_t)std::max<size_t>(1, std::min<size_t>(work_budget / per_item, 1 << 16)) : 1;
@@ -564,7 +580,8 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
     if (B < 1) return MCTRG_ENOMEM;
     CK(o_tflags.ensure(sizeof(uint32_t) * (size_t)B));
     CK(lnacc.ensure(sizeof(double) * (size_t)B));
-    const int grid_s = 1024;
+    const int grid_s = run_sample_grid(lv, s0, nlev, chi);
+    const int ks = kept_stride(chi);
     size_t max_h = 0, max_items = 0, max_xy = 0, max_m = 0, max_w = 0, max_np = 0, max_scr = 0;
     for (int k = s0; k < nlev; ++k) {
       const LevelInfo& a = lv[k];
@@ -608,15 +625,15 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
         const LevelInfo& a = lv[k];
         if (!use_bidiag(a.n, lv[k - 1].D * lv[k - 1].D)) continue;
         bd_n = std::max(bd_n, (size_t)a.n);
-        bd_scr = std::max(bd_scr, bd_vectors_scratch_doubles(a.n, (int)std::min<int64_t>(S, 1 << 16)));
+        bd_scr = std::max(bd_scr, bd_vectors_scratch_doubles(a.n, (int)std::min<int64_t>(S, 1 << 16), a.kc));
       }
       if (bd_n) {
         const size_t Ss = (size_t)std::max<int64_t>(S, 1);
         CK(bdb.ensure(sizeof(double) * Ss * 3 * bd_n));
-        CK(keptb.ensure(sizeof(int) * Ss * 32));
-        CK(sigtb.ensure(sizeof(double) * Ss * 32));
+        CK(keptb.ensure(sizeof(int) * Ss * ks));
+        CK(sigtb.ensure(sizeof(double) * Ss * ks));
         CK(nkb.ensure(sizeof(int) * Ss));
-        CK(vrowsb.ensure(sizeof(double) * Ss * 32 * bd_n));
+        CK(vrowsb.ensure(sizeof(double) * Ss * ks * bd_n));
         CK(bdscr.ensure(sizeof(double) * bd_scr));
       }
     }
@@ -790,15 +807,16 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
               return launch_bd_bisect(bdb.as<double>(), a.n, a.n_pad, (int)Si, sigb.as<double>(), permb.as<int>(),
                                       nnzb.as<int>(), ilns1.as<double>() + i0, zero_rel, st); }));
             sa.mode = 1; sa.kept = keptb.as<int>(); sa.sigt = sigtb.as<double>(); sa.nk = nkb.as<int>();
+            sa.kstride = ks;
             sa.W = nullptr; sa.perm = permb.as<int>();
-            CK(timed(MCTRG_K_SAMPLE, Si, Si * 4.0 * nn * a.kc, 8.0 * Si * (a.n_pad + 2.0 * 32),
+            CK(timed(MCTRG_K_SAMPLE, Si, Si * 4.0 * nn * a.kc, 8.0 * Si * (a.n_pad + 2.0 * ks),
                      [&] { return launch_sample_split(sa, st, grid_s); }));
             BdVecArgs va{};
             va.bd = bdb.as<double>(); va.R = Wb.as<double>(); va.sig = sigb.as<double>(); va.kept = keptb.as<int>();
             va.nk = nkb.as<int>(); va.vrows = vrowsb.as<double>(); va.scratch = bdscr.as<double>();
-            va.n = a.n; va.n_pad = a.n_pad; va.S = (int)Si; va.kmax = a.kc;
+            va.n = a.n; va.n_pad = a.n_pad; va.S = (int)Si; va.kmax = a.kc; va.kstride = ks;
             CK(timed(MCTRG_K_VECTORS, Si, Si * (2.0 * nn * nn * a.kc + 40.0 * nn * a.kc),
-                     8.0 * Si * (nn * nn / 2.0 + 3.0 * nn + 2.0 * 32 * nn), [&] { return launch_bd_vectors(va, st); }));
+                     8.0 * Si * (nn * nn / 2.0 + 3.0 * nn + 2.0 * a.kc * nn), [&] { return launch_bd_vectors(va, st); }));
             sa.mode = 2; sa.vrows = vrowsb.as<double>();
             CK(timed(MCTRG_K_SAMPLE, Si, Si * 2.0 * nn * nn * a.kc, 8.0 * Si * (2.0 * nn * nn + 2.0 * nn * a.kc),
                      [&] { return launch_sample_split(sa, st, grid_s); }));

@@ -10,6 +10,10 @@
 
 namespace mctrg {
 
+// Largest kept count: a level matrix is at most chi^2 = 2304 on a side (the
+// bidiagonalization route's limit), the sampler and the vectors take up to 64.
+constexpr int kMaxChi = 48;
+
 // A device allocation that only grows.
 struct DevBuf {
   void* p = nullptr;

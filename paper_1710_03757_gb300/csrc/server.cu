@@ -227,7 +227,7 @@ extern "C" int mctrg_server_submit(mctrg_server_t s, double beta, double h, int 
                                    double target_se_lnZ, int64_t max_samples, uint64_t seed,
                                    uint64_t* job_id) {
   if (!s || !job_id) return MCTRG_EINVAL;
-  if (L < 2 || (L & (L - 1)) || L > 65536 || chi < 1 || chi > 32 || !(beta >= 0) ||
+  if (L < 2 || (L & (L - 1)) || L > 65536 || chi < 1 || chi > mctrg::kMaxChi || !(beta >= 0) ||
       !std::isfinite(beta) || !std::isfinite(h) || !(target_se_lnZ >= 0) || max_samples < 1 ||
       (uint64_t)max_samples > (1ull << 32))
     return MCTRG_EINVAL;
@@ -298,7 +298,7 @@ extern "C" int mctrg_server_wait(mctrg_server_t s, uint64_t job_id, double timeo
 }
 
 extern "C" int mctrg_server_footprint(mctrg_server_t s, int L, int chi, int64_t max_samples, size_t* bytes) {
-  if (!s || !bytes || L < 2 || (L & (L - 1)) || L > 65536 || chi < 1 || chi > 32 || max_samples < 1)
+  if (!s || !bytes || L < 2 || (L & (L - 1)) || L > 65536 || chi < 1 || chi > mctrg::kMaxChi || max_samples < 1)
     return MCTRG_EINVAL;
   int64_t B = 0, S = 0;
   size_t total = 0;

@@ -38,20 +38,20 @@ cudaError_t svd_chunk(const double* M, int n, int64_t count, double* sigma, doub
   return cudaGetLastError();
 }
 
-// Kept ranks 0 .. nv-1 for every matrix (the leading right vectors).
-__global__ void k_kept_leading(int* kept, int* nk, const int* nnz, int nv, int S) {
+// Kept ranks 0 .. nv-1 for every matrix (the leading right vectors), stride ks.
+__global__ void k_kept_leading(int* kept, int* nk, const int* nnz, int nv, int S, int ks) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
-  for (int q = 0; q < 32; ++q) kept[(size_t)s * 32 + q] = q < nv ? q : 0;
+  for (int q = 0; q < ks; ++q) kept[(size_t)s * ks + q] = q < nv ? q : 0;
   nk[s] = nv;
 }
 
 __global__ void k_bd_finalize(const double* sig, int n, int n_pad, int nv, const double* vrows, double* sigma,
-                              double* vt) {
+                              double* vt, int ks) {
   const int64_t b = blockIdx.x;
   for (int r = threadIdx.x; r < n; r += blockDim.x) sigma[b * n + r] = sig[b * n_pad + r];
   if (!vt) return;
-  for (int64_t e = threadIdx.x; e < (int64_t)nv * n; e += blockDim.x) vt[b * nv * n + e] = vrows[b * 32 * n + e];
+  for (int64_t e = threadIdx.x; e < (int64_t)nv * n; e += blockDim.x) vt[b * nv * n + e] = vrows[b * ks * n + e];
 }
 
 }  // namespace mctrg
@@ -60,27 +60,28 @@ using namespace mctrg;
 
 extern "C" int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, double* sigma, int n_vec,
                                         double* vt, void* stream) {
-  if (!M || !sigma || n < 2 || n > 1024 || batch < 1 || batch > (1 << 30)) return MCTRG_EINVAL;
-  if (n_vec < 0 || n_vec > 32 || n_vec > n || (n_vec > 0 && !vt)) return MCTRG_EINVAL;
+  if (!M || !sigma || n < 2 || n > 2304 || batch < 1 || batch > (1 << 30)) return MCTRG_EINVAL;
+  if (n_vec < 0 || n_vec > kKeptMax || n_vec > n || (n_vec > 0 && !vt)) return MCTRG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const int np = n + (n & 1);
-  const size_t per = ((size_t)n * n + 3 * (size_t)n + np + 32 * (size_t)n) * sizeof(double) +
-                     ((size_t)np + 1 + 33) * sizeof(int);
+  const int ks = kept_stride(n_vec);
+  const size_t per = ((size_t)n * n + 3 * (size_t)n + np + (size_t)ks * n) * sizeof(double) +
+                     ((size_t)np + 1 + ks + 1) * sizeof(int);
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return MCTRG_ECUDA;
   const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>({batch, (int64_t)(fr / 4 / per), 1 << 16}));
-  const size_t scr = bd_vectors_scratch_doubles(n, (int)chunk) * sizeof(double);
+  const size_t scr = bd_vectors_scratch_doubles(n, (int)chunk, std::max(1, n_vec)) * sizeof(double);
   void* buf = nullptr;
   if (cudaMalloc(&buf, per * (size_t)chunk + scr) != cudaSuccess) return MCTRG_ENOMEM;
   double* W = (double*)buf;
   double* bd = W + (size_t)chunk * n * n;
   double* sig = bd + (size_t)chunk * 3 * n;
   double* vrows = sig + (size_t)chunk * np;
-  double* scratch = vrows + (size_t)chunk * 32 * n;
+  double* scratch = vrows + (size_t)chunk * ks * n;
   int* perm = (int*)(scratch + scr / sizeof(double));
   int* nnz = perm + (size_t)chunk * np;
   int* kept = nnz + chunk;
-  int* nk = kept + (size_t)chunk * 32;
+  int* nk = kept + (size_t)chunk * ks;
   int status = MCTRG_OK;
   for (int64_t b0 = 0; b0 < batch; b0 += chunk) {
     const int cnt = (int)std::min(chunk, batch - b0);
@@ -89,15 +90,15 @@ extern "C" int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, d
     cudaError_t e = launch_bidiag(ba, st);
     if (e == cudaSuccess) e = launch_bd_bisect(bd, n, np, cnt, sig, perm, nnz, nullptr, 0.0, st);
     if (e == cudaSuccess && n_vec > 0) {
-      k_kept_leading<<<(cnt + 127) / 128, 128, 0, st>>>(kept, nk, nnz, n_vec, cnt);
+      k_kept_leading<<<(cnt + 127) / 128, 128, 0, st>>>(kept, nk, nnz, n_vec, cnt, ks);
       BdVecArgs va{};
       va.bd = bd; va.R = W; va.sig = sig; va.kept = kept; va.nk = nk; va.vrows = vrows; va.scratch = scratch;
-      va.n = n; va.n_pad = np; va.S = cnt; va.unit_rows = 1; va.kmax = n_vec;
+      va.n = n; va.n_pad = np; va.S = cnt; va.unit_rows = 1; va.kmax = n_vec; va.kstride = ks;
       e = launch_bd_vectors(va, st);
     }
     if (e == cudaSuccess) {
       k_bd_finalize<<<cnt, 256, 0, st>>>(sig, n, np, n_vec, vrows, sigma + (size_t)b0 * n,
-                                          n_vec > 0 ? vt + (size_t)b0 * n_vec * n : nullptr);
+                                          n_vec > 0 ? vt + (size_t)b0 * n_vec * n : nullptr, ks);
       e = cudaGetLastError();
     }
     if (e != cudaSuccess) { status = MCTRG_ECUDA; break; }

@@ -94,6 +94,32 @@ def test_values_and_kept_vectors_against_lapack(torch, n, kind):
                 assert abs(np.linalg.norm(proj) - 1.0) <= 1e-10
 
 
+@pytest.mark.parametrize("n,kind,nv", [(1040, "lowrank", 48), (1600, "gauss", 40), (1600, "graded", 40),
+                                       (1600, "pairs", 40), (2304, "gauss", 64)])
+def test_wide_values_and_vectors_against_lapack(torch, n, kind, nv):
+    # sides above 1024 take the streamed form of the reduction; 64 kept vectors
+    # take two warps of inverse iteration and, at n = 2304, back-transformation
+    # groups of 8
+    A = _matrices(n, 1, kind, seed=3000 + n + len(kind))
+    sg, V = _run(torch, A, nv)
+    _, ref, Vr = np.linalg.svd(A[0])
+    s1 = ref[0]
+    np.testing.assert_allclose(sg[0], ref, atol=1e-13 * s1 * n ** 0.5, rtol=0)
+    kv = int(np.sum(sg[0][:nv] > 1e-10 * s1))
+    Vb = V[0][:kv]
+    np.testing.assert_allclose(Vb @ Vb.T, np.eye(kv), atol=1e-12)
+    R = A[0].T @ (A[0] @ Vb.T) - Vb.T * sg[0][:kv] ** 2
+    assert np.abs(R).max() <= 1e-12 * s1 * s1
+    for r in range(kv):
+        gap = min([abs(ref[r] - ref[q]) for q in (r - 1, r + 1) if 0 <= q < n] + [np.inf])
+        if gap > 1e-3 * s1 and ref[r] > 1e-6 * s1:
+            err = min(np.linalg.norm(Vb[r] - Vr[r]), np.linalg.norm(Vb[r] + Vr[r]))
+            assert err <= 1e-12 + 1e-13 * s1 / gap
+        else:
+            C = [q for q in range(n) if abs(ref[q] - ref[r]) <= 2e-3 * s1]
+            assert abs(np.linalg.norm(Vr[C] @ Vb[r]) - 1.0) <= 1e-10
+
+
 def test_zero_and_tiny_matrices(torch):
     A = np.zeros((3, 8, 8))
     A[1, 0, 0] = 1e-300                  # far below the underflow guard's range
@@ -120,6 +146,18 @@ def test_generic_tensor_parity_bidiag(torch, L, chi, D, n):
     gpu = gpu_run(L, chi, n, seed, T0=T0, svd=mctrg.SVD_BIDIAG)
     orc = run_many(Problem(T0, L, chi), seed, 0, n)
     assert compare(gpu, orc, min_ok=0.9, label="bidiag generic L%d chi%d D%d" % (L, chi, D)) >= 0.9 * n
+
+
+def test_chi48_generic_parity(torch):
+    # D = 7 generic tensor, chi = 48 on L = 2: 48 of the 49 values of level 0
+    # are sampled (two lane sets of the sampler tables), then level 1 has
+    # 2304 x 2304 matrices of rank <= 49 (streamed reduction, 48 kept vectors:
+    # two warps of inverse iteration, back-transformation groups of 8)
+    T0 = generic_tensor(7, seed=4807)
+    seed = 0x48
+    gpu = gpu_run(2, 48, 8, seed, T0=T0)
+    orc = run_many(Problem(T0, 2, 48), seed, 0, 8, workers=8)
+    compare(gpu, orc, min_ok=0.5, label="generic D7 L2 chi48")
 
 
 @pytest.mark.parametrize("beta,h,L,chi,n", [(0.3, 0.1, 8, 4, 100), (0.44, 0.05, 8, 2, 200)])
