@@ -204,6 +204,34 @@ int mctrg_init_impurity(mctrg_ctx_t ctx, double beta, double h, int L, int chi, 
  * (denominator mean <= 0). */
 int mctrg_ratio_estimate(const mctrg_estimate* num, const mctrg_estimate* den, double* ratio, double* se);
 
+/* Monte Carlo HOTRG: the stochastic truncation of Sec. II on the higher-order
+ * TRG (Xie et al. 2012), one of the other SVD-based coarse-graining schemes
+ * to which Secs. III and V say the method extends.  A step merges pairs of
+ * rows: T(x,2j) over T(x,2j+1), contracted over their vertical bond, gives
+ * M(x,j) with horizontal legs of dimension Dh^2.  Every merged horizontal
+ * bond gets its own random projector P~ = sum_{i in e} u_i u_i^T / r_i from
+ * the eigenpairs (u_i, lambda_i) of the Gram matrix of M(x,j)'s right
+ * unfolding: e is a chi-subset of the nonzero eigenvalues (above n 2^-52
+ * lambda_1) drawn with p(e) ~ prod lambda_i, r_i its inclusion rates, so
+ * E[P~] is the identity on all that M(x,j) sees and every trajectory is an
+ * unbiased sample of Z (sign tracked).  The new tensor is
+ * U~_left^T M U~_right (U~ = [u_i / sqrt(r_i)]) divided by sqrt(lambda_1) of
+ * its right bond; the lattice is then reflected across its diagonal, so after
+ * 2 log2 L steps one tensor is left and traced.  Trajectory i draws its
+ * uniforms from Philox4x32-10 under seed with counter (t >> 1, bond, step,
+ * first_traj + i), bond = j Lx + x.
+ * T0: NULL for the Ising site tensor at (beta, h) (that of mctrg_init_lattice),
+ * else a host pointer to D^4 doubles [l][u][r][d], 2 <= D <= 8 (beta, h
+ * ignored).  L a power of two, 2 <= L <= 4096; 2 <= chi <= 32.  opt: device,
+ * cuda_stream, hbm_budget_bytes (0: 70% of the free memory), max_chunk (> 0:
+ * at most that many trajectories at once).  Outputs as mctrg_run (each host
+ * or device memory, NULL to skip; est required).  Allocates its working
+ * memory and frees it before returning; blocks until done.  Returns OK,
+ * EDOMAIN (mean <= 0), EINVAL, ENOMEM, ECUDA. */
+int mctrg_hotrg_run(const mctrg_options* opt, double beta, double h, const double* T0, int D, int L, int chi,
+                    int64_t n_samples, uint64_t seed, uint64_t first_traj, double* lnabsZ, int8_t* sign,
+                    uint8_t* flags, mctrg_estimate* est);
+
 /* Same as mctrg_init_lattice with an arbitrary site tensor T0 (host pointer,
  * D^4 doubles, index order [l][u][r][d], row-major), 1 <= D <= 8, copied. */
 int mctrg_init_tensor(mctrg_ctx_t ctx, const double* T0, int D, int L, int chi);

@@ -25,7 +25,7 @@ EXPORTS = [
     "mctrg_reset_kernel_stats", "mctrg_svd_batched", "mctrg_svd_batched_noalloc",
     "mctrg_svd_bidiag_batched", "mctrg_measure_fp64_peak", "mctrg_contract_batched",
     "mctrg_server_footprint", "mctrg_server_memory", "mctrg_batch_run", "mctrg_init_impurity",
-    "mctrg_ratio_estimate",
+    "mctrg_ratio_estimate", "mctrg_hotrg_run",
 ]
 K_FORM_XY, K_GEMM, K_JACOBI, K_SAMPLE, K_TRACE, K_OTHER, K_BIDIAG, K_BISECT, K_VECTORS, K_COUNT = range(10)
 KERNEL_NAMES = ["form_xy", "gemm", "jacobi", "sample_split", "trace", "other", "bidiag", "bisect", "vectors"]
@@ -84,6 +84,8 @@ def lib():
             "mctrg_ratio_estimate": (c_int, [ctypes.POINTER(Estimate), ctypes.POINTER(Estimate),
                                              ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
             "mctrg_run": (c_int, [vp, i64, u64, u64, vp, vp, vp, ctypes.POINTER(Estimate)]),
+            "mctrg_hotrg_run": (c_int, [ctypes.POINTER(Options), c_double, c_double, vp, c_int, c_int, c_int, i64,
+                                        u64, u64, vp, vp, vp, ctypes.POINTER(Estimate)]),
             "mctrg_footprint": (c_int, [vp, i64, ctypes.POINTER(ctypes.c_size_t)]),
             "mctrg_merge_estimates": (c_int, [ctypes.POINTER(Estimate), c_int, ctypes.POINTER(Estimate)]),
             "mctrg_destroy": (None, [vp]),
@@ -207,6 +209,26 @@ def mctrg_run(ctx, n_samples, seed, first_traj=0, lnabsZ=None, sign=None, flags=
     est = Estimate()
     s = lib().mctrg_run(ctx, int(n_samples), int(seed), int(first_traj), _ptr(lnabsZ), _ptr(sign),
                         _ptr(flags), ctypes.byref(est))
+    return s, est
+
+
+def mctrg_hotrg_run(opt, L, chi, n_samples, seed, first_traj=0, beta=0.0, h=0.0, T0=None, lnabsZ=None,
+                    sign=None, flags=None):
+    """Monte Carlo HOTRG trajectories; T0 None for the Ising site tensor at
+    (beta, h).  Returns (status, Estimate)."""
+    import numpy as np
+    est = Estimate()
+    if T0 is None:
+        tp, D = None, 2
+    else:
+        T0 = np.ascontiguousarray(T0, dtype=np.float64)
+        D = T0.shape[0]
+        if T0.size != D ** 4:
+            raise ValueError("T0 must hold D^4 values")
+        tp = T0.ctypes.data
+    s = lib().mctrg_hotrg_run(ctypes.byref(opt), float(beta), float(h), tp, int(D), int(L), int(chi),
+                              int(n_samples), int(seed), int(first_traj), _ptr(lnabsZ), _ptr(sign), _ptr(flags),
+                              ctypes.byref(est))
     return s, est
 
 
