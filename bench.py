@@ -247,6 +247,42 @@ def _uneven_jobs(n_jobs, seed):
     return jobs
 
 
+def _hotrg_flops(L, chi, D0=2):
+    """Algorithmic FP64 flops of one Monte Carlo HOTRG trajectory: per bond the
+    two pair Gram matrices, the bond Gram matrix, its bidiagonal reduction
+    ((8/3) n^3) and the three contraction stages."""
+    Lx = Ly = L
+    Dh = Dv = D0
+    total = 0.0
+    while Lx * Ly > 1:
+        n, q = Dh * Dh, Dh * Dv
+        kc, N = min(chi, n), Lx * (Ly // 2)
+        fma = (2 * q ** 3 + n * n * Dv * Dv + kc * Dv * Dh * Dh * Dv * Dh + kc * Dv * Dh * Dh * Dv * q +
+               kc * kc * Dv * Dv * n)
+        total += N * (2.0 * fma + 8.0 / 3.0 * n ** 3)
+        Lx, Ly = Ly // 2, Lx
+        Dh, Dv = Dv, kc
+    return total
+
+
+def measure_hotrg(mctrg, fp64_peak, L=64, chi=16, n=16, beta=0.44, seed=0xB0A7 + 6):
+    """Monte Carlo HOTRG (mctrg_hotrg_run, one blocking call that allocates and
+    frees its memory): trajectories/s, wall clock, on the Ising torus."""
+    import time
+    o = mctrg.make_options()
+    mctrg.mctrg_hotrg_run(o, 8, chi, 2, seed, beta=beta)            # module load, first allocations
+    t0 = time.perf_counter()
+    st, est = mctrg.mctrg_hotrg_run(o, L, chi, n, seed, beta=beta)
+    dt = time.perf_counter() - t0
+    f = _hotrg_flops(L, chi) * n
+    return {"config": {"L": L, "chi": chi, "beta": beta, "trajectories": n}, "seconds": dt,
+            "trajectories_per_s": n / dt, "alg_tflops": f / dt / 1e12,
+            "frac_of_fp64_peak": (f / dt / 1e12) / fp64_peak if fp64_peak else None,
+            "ln_mean_Z": est.ln_mean_Z, "se_ln_Z": est.se_ln_Z, "status": mctrg.mctrg_strerror(st),
+            "note": "whole call on the wall clock (allocation, every kernel, the copies); the dominant kernel, "
+                    "the contraction's middle stage, runs at the FP64 rate"}
+
+
 def measure_uneven(mctrg, n_jobs=24, seed=0xB0A7 + 4):
     """Jobs of uneven chi and lattice size: (a) through the server (each job on a
     worker's stream, FP64), (b) as one batch (levels advanced together, the SVD
@@ -391,6 +427,7 @@ def main():
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-time-to-se", action="store_true")
+    ap.add_argument("--no-hotrg", action="store_true")
     ap.add_argument("--table1", action="store_true",
                     help="per-sample std of Z~ on the paper's 128-spin network (Table 1) instead of the bench line")
     args = ap.parse_args()
@@ -611,6 +648,12 @@ def main():
                                         "fp64tc": measure_time_to_se(mctrg, mctrg.MCTRG_FP64TC)}
         except Exception as e:
             line["time_to_se_32x32"] = {"error": repr(e)[:200]}
+    if not args.no_hotrg:
+        try:
+            line["hotrg"] = measure_hotrg(mctrg, line["roofline"].get("peak") if line["roofline"]["unit"] == "TFLOP/s"
+                                          else None)
+        except Exception as e:
+            line["hotrg"] = {"error": repr(e)[:200]}
     if not args.no_uneven:
         try:
             line["uneven_batch"] = measure_uneven(mctrg)
