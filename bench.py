@@ -338,11 +338,11 @@ def _time_to_se(est, rate, targets=(1e-1, 1e-2)):
     return out
 
 
-def measure_time_to_se(mctrg, precision=0, L=32, chi=16, beta=0.44, n=2048, target=1e-3):
+def measure_time_to_se(mctrg, precision=0, L=32, chi=16, beta=0.44, n=2048, target=1e-3, svd=0):
     """Time to a stated standard error of ln Z on the 32 x 32 lattice (chi = 16): n
     trajectories, their SE, the trajectories the target needs by the 1/sqrt(N) law and the
     time at the measured rate (this lattice's estimator is well behaved: ESS near n)."""
-    ctx = mctrg.mctrg_create(mctrg.make_options(precision=precision))
+    ctx = mctrg.mctrg_create(mctrg.make_options(precision=precision, svd=svd))
     try:
         assert mctrg.mctrg_init_lattice(ctx, beta, 0.0, L, chi) == 0
         mctrg.mctrg_run(ctx, 64, 0x5E, 10 ** 6)             # warm
@@ -471,8 +471,10 @@ def main():
     B = wl["traj_per_step"]
     seed = 0x4D435452 + 2
 
-    def make_ctx(prec):
-        opts = mctrg.make_options(device=local, stream=stream.cuda_stream, precision=prec, profile=1)
+    def make_ctx(prec, svd=None):
+        if svd is None:   # FP64TC takes the tensor-core SVD route too
+            svd = mctrg.SVD_BAND if prec == mctrg.MCTRG_FP64TC else mctrg.SVD_AUTO
+        opts = mctrg.make_options(device=local, stream=stream.cuda_stream, precision=prec, profile=1, svd=svd)
         c = mctrg.mctrg_create(opts)
         s = mctrg.mctrg_init_lattice(c, wl["beta"], wl["h"], wl["L"], wl["chi"])
         if s != 0:
@@ -534,10 +536,13 @@ def main():
         for name, prec, note, ratio in (
                 ("tf32x3", mctrg.MCTRG_TF32X3, "TF32 hi/lo split, three tcgen05 passes, FP32 accumulation", 0.5),
                 ("fp64tc", mctrg.MCTRG_FP64TC, "BF16 slices multiplied exactly on tcgen05, summed in FP64 "
-                                               "(Ozaki scheme)", 1.0)):
+                                               "(Ozaki scheme), in the contraction and in the SVD's dense -> "
+                                               "band reduction (8-bit digits of a fixed-point trailing matrix)",
+                 1.0)):
             cm = make_ctx(prec)
             ms_m, ests_m, outs_m = timed_steps(cm, args.steps, 1, 0)
             gst = mctrg.mctrg_kernel_stats(cm, mctrg.K_GEMM)
+            kst = [mctrg.mctrg_kernel_stats(cm, k) for k in range(mctrg.K_COUNT)]
             mctrg.mctrg_destroy(cm)
             got = np.concatenate([o[0].cpu().numpy() for o in outs_m])
             # near-tie trajectories (flagged in either run) may keep different indices: left out,
@@ -567,7 +572,22 @@ def main():
                                 "tensor_tflops": tc_rate, "tensor_peak_tflops": tc_peak,
                                 "tensor_frac": tc_rate / tc_peak if tc_rate else None,
                                 "peak_note": "MEASURED_PEAKS bf16 sustained" + (" x 1/2 (TF32 nominal ratio)"
-                                                                                if ratio != 1.0 else "")}}
+                                                                                if ratio != 1.0 else "")},
+                "kernels": {mctrg.KERNEL_NAMES[k]: {"launches": kst[k].launches, "ms": round(kst[k].ms, 3),
+                                                     "share": round(kst[k].ms / max(1e-9, sum(x.ms for x in kst)),
+                                                                    4)}
+                            for k in range(mctrg.K_COUNT) if kst[k].launches}}
+            bs = kst[mctrg.K_BAND]
+            if bs.launches and bs.ms > 0:
+                # the reduction's algorithmic (8/3) n^3 FP64 flops per matrix over its time:
+                # the rate the FP64 pipe would need to match it
+                eq = bs.flops_alg / (bs.ms / 1e3) / 1e12
+                fpk = fp64_peak if pst == 0 and fp64_peak > 0 else FP64_NOMINAL_TFLOPS
+                mixed[name]["svd_band_stage"] = {
+                    "launches": bs.launches, "avg_launch_ms": bs.ms / bs.launches,
+                    "fp64_equivalent_tflops": eq, "fp64_peak_tflops": fpk, "frac_of_fp64_peak": eq / fpk,
+                    "note": "dense -> band reduction (tensor-core digit products, FP64 panels): algorithmic "
+                            "(8/3) n^3 flops per matrix / time, against the FP64 pipe's measured peak"}
     ms_t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -645,7 +665,8 @@ def main():
     if not args.no_time_to_se:
         try:
             line["time_to_se_32x32"] = {"fp64": measure_time_to_se(mctrg, 0),
-                                        "fp64tc": measure_time_to_se(mctrg, mctrg.MCTRG_FP64TC)}
+                                        "fp64tc": measure_time_to_se(mctrg, mctrg.MCTRG_FP64TC,
+                                                                     svd=mctrg.SVD_BAND)}
         except Exception as e:
             line["time_to_se_32x32"] = {"error": repr(e)[:200]}
     if not args.no_hotrg:

@@ -118,8 +118,8 @@ typedef struct {
                                  were timed); NULL = choose every run, keep nothing */
 } mctrg_options;
 
-/* Route of the per-trajectory SVDs (Sec. II, Eq. exactSVD), both FP64 with
- * the absolute accuracy of a backward-stable SVD (a few eps |M|):
+/* Route of the per-trajectory SVDs (Sec. II, Eq. exactSVD), all with the
+ * absolute accuracy of a backward-stable FP64 SVD (a few eps |M|):
  *   JACOBI  QR with column pivoting, then one-sided Jacobi on the rows; its
  *           cost follows the numerical rank.
  *   BIDIAG  Householder bidiagonalization, every singular value by bisection
@@ -128,9 +128,14 @@ typedef struct {
  *           (8/3) n^3 + O(n^2) flops whatever the rank.
  *   AUTO    BIDIAG where the matrices can have full rank (n >= 64 and the
  *           plaquette's inner dimension d^2 >= n / 2), JACOBI elsewhere.
+ *   BAND    AUTO's choice, with the two-stage route in place of BIDIAG where
+ *           n is a multiple of 8 from 64 to 256 (chi <= 16): the reduction's
+ *           (8/3) n^3 flops as exact integer products of 8-bit digit slices
+ *           on the tensor cores, O(n^2) FP64 work per matrix beside them
+ *           (mctrg_svd_band_batched).  Not taken by mctrg_batch_run (EINVAL).
  * JACOBI covers n <= 1024: levels with larger matrices (n up to 2304, chi up
  * to 48) take BIDIAG whatever the option. */
-typedef enum { MCTRG_SVD_AUTO = 0, MCTRG_SVD_JACOBI = 1, MCTRG_SVD_BIDIAG = 2 } mctrg_svd_route;
+typedef enum { MCTRG_SVD_AUTO = 0, MCTRG_SVD_JACOBI = 1, MCTRG_SVD_BIDIAG = 2, MCTRG_SVD_BAND = 3 } mctrg_svd_route;
 
 /* Estimate of Z from n trajectories (Sec. III Eq. infiniteEnsemble, Sec. V Eq.
  * shrunkDev).  With m = ln_scale = max_i ln|Z~_i| and x_i = sign_i e^{ln|Z~_i| - m}:
@@ -270,12 +275,16 @@ int mctrg_merge_estimates(const mctrg_estimate* parts, int k, mctrg_estimate* ou
  *   BISECT   no flop count is recorded: each nonzero value takes ~20 FP32 and
  *            ~6 FP64 Sturm counts of 2n steps (2 FP64 operations per step)
  *   VECTORS  2 n^2 kc + 20 (2n) kc per matrix (back-transformation and
- *            inverse iteration of the kept vectors)
+ *            inverse iteration of the kept vectors; 4 n^2 kc on the BAND route,
+ *            whose vectors pass back through both stages)
+ *   BAND     (8/3) n^3 per matrix (the dense -> band reduction of the BAND
+ *            route: tensor-core products and FP64 panel factorizations)
+ *   CHASE    6 b n^2 per matrix, b = 8 (band -> bidiagonal bulge chase)
  * bytes_alg counts each kernel's compulsory global-memory traffic
  * (inputs read once, outputs written once). */
 enum { MCTRG_K_FORM_XY = 0, MCTRG_K_GEMM = 1, MCTRG_K_JACOBI = 2, MCTRG_K_SAMPLE = 3,
        MCTRG_K_TRACE = 4, MCTRG_K_OTHER = 5, MCTRG_K_BIDIAG = 6, MCTRG_K_BISECT = 7,
-       MCTRG_K_VECTORS = 8, MCTRG_K_COUNT = 9 };
+       MCTRG_K_VECTORS = 8, MCTRG_K_BAND = 9, MCTRG_K_CHASE = 10, MCTRG_K_COUNT = 11 };
 typedef struct {
     int64_t launches;
     double ms;          /* summed event-timed duration */
@@ -393,6 +402,34 @@ int mctrg_contract_batched(const double* X, const double* Yt, int D, int K, int6
  * 2 <= n <= 2304, 0 <= n_vec <= min(64, n).  Errors: EINVAL, ENOMEM, ECUDA. */
 int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, double* sigma, int n_vec,
                              double* vt, void* stream);
+
+/* The two-stage (band) route of the same SVD on its own (the route
+ * MCTRG_SVD_BAND of the contexts).  Sec. II asks only for the SVD of each
+ * matricization; this route computes it with the reduction's flops on the
+ * tensor cores: M is reduced to an upper band with 8 superdiagonals in
+ * panels of 8 columns (QR of each column panel and LQ of its row panel in
+ * FP64; the products with the trailing matrix, and its two-sided update, as
+ * exact integer products of 8-bit digit slices on the tensor cores, the
+ * trailing matrix held in 59-bit fixed point relative to |M|_F), the band is
+ * reduced to bidiagonal form by bulge chasing (FP64), and the singular values
+ * and right vectors follow as in mctrg_svd_bidiag_batched (bisection,
+ * inverse iteration, and the two stages' right reflectors applied back).
+ * Arguments, layouts, accuracy and ownership as mctrg_svd_bidiag_batched;
+ * n a multiple of 8 with 64 <= n <= 256, 0 <= n_vec <= 16.
+ * Errors: EINVAL, ENOMEM, ECUDA (also when a tensor-core kernel's bounded
+ * wait expired). */
+int mctrg_svd_band_batched(const double* M, int n, int64_t batch, double* sigma, int n_vec,
+                           double* vt, void* stream);
+
+/* The band route's reductions alone, for inspection: band (device,
+ * batch*n*9) receives the upper band B(i, i+o), o = 0..8 (entries beyond
+ * column n-1 undefined), an orthogonal two-sided transformation of M; bd
+ * (device, batch*3n, or NULL to stop after the band) the diagonal d (n) and
+ * superdiagonal e (n, e[n-1] = 0) of the bidiagonal the bulge chase reaches,
+ * then n zeros.  The paper has no counterpart (the steps of an SVD).  n and
+ * batch as mctrg_svd_band_batched.  Allocates and frees its working memory.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int mctrg_band_reduce_batched(const double* M, int n, int64_t batch, double* band, double* bd, void* stream);
 
 /* ---- measurement ------------------------------------------------------ *
  * FP64 arithmetic rate of a device, the peak against which the FP64 kernels

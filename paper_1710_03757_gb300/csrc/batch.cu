@@ -571,6 +571,7 @@ extern "C" int mctrg_batch_run(const mctrg_options* opt, const mctrg_job* jobs, 
                                double* lnabsZ, int8_t* sign, uint8_t* flags) {
   if (!opt || !jobs || !est || n_jobs < 1) return MCTRG_EINVAL;
   if (opt->precision != MCTRG_FP64 && opt->precision != MCTRG_FP64TC) return MCTRG_EINVAL;
+  if (opt->svd == MCTRG_SVD_BAND) return MCTRG_EINVAL;   // ragged launches take the one-stage route
   for (int j = 0; j < n_jobs; ++j) {
     const mctrg_job& b = jobs[j];
     if (b.n_samples < 1 || b.first_traj + (uint64_t)b.n_samples > (1ull << 32)) return MCTRG_EINVAL;

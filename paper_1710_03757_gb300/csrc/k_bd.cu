@@ -1067,7 +1067,7 @@ cudaError_t launch_bd_vectors(const BdVecArgs& a, cudaStream_t st) {
   const int ls = invit_stride(a.kmax);
   k_bd_invit<<<invit_slots(a.n, a.S, a.kmax), ls > 32 ? 64 : 32, 0, st>>>(a, ls);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || a.skip_backtr) return e;
   static std::atomic<uint64_t> attr{0};
   e = raise_smem_limit(k_bd_backtr, kSmemCap, attr);
   if (e != cudaSuccess) return e;

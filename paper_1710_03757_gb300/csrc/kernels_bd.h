@@ -75,6 +75,7 @@ struct BdVecArgs {
   int kmax;             // largest nk of the batch (<= 64)
   int kstride;          // kept_stride of the largest kept count (non-ragged layout)
   const SvdItem* items = nullptr;   // ragged: S matrices described here (n = the largest)
+  int skip_backtr = 0;  // 1: leave the unit vectors of the bidiagonal in vrows
 };
 cudaError_t launch_bd_vectors(const BdVecArgs& a, cudaStream_t st);
 size_t bd_vectors_scratch_doubles(int n, int S, int kmax);

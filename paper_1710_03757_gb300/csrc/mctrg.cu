@@ -18,6 +18,7 @@
 #include "../../include/mctrg.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "kernels_band.h"
 #include "kernels_bd.h"
 #include "kernels_tc.h"
 #include "mctrg_internal.h"
@@ -78,7 +79,7 @@ extern "C" int mctrg_options_default(mctrg_options* opt) {
 extern "C" int mctrg_create(const mctrg_options* opt, mctrg_ctx_t* out) {
   if (!opt || !out) return MCTRG_EINVAL;
   if (opt->precision < MCTRG_FP64 || opt->precision > MCTRG_FP64TC) return MCTRG_EINVAL;
-  if (opt->svd < MCTRG_SVD_AUTO || opt->svd > MCTRG_SVD_BIDIAG) return MCTRG_EINVAL;
+  if (opt->svd < MCTRG_SVD_AUTO || opt->svd > MCTRG_SVD_BAND) return MCTRG_EINVAL;
   if (!(opt->zero_tol_scale >= 0.0) || !std::isfinite(opt->zero_tol_scale)) return MCTRG_EINVAL;
   if (opt->deterministic_levels < 0) return MCTRG_EINVAL;
   *out = nullptr;
@@ -165,7 +166,8 @@ size_t mctrg_ctx::held_bytes() const {
   const DevBuf* all[] = {&T0, &shM, &shW, &shSig, &shPerm, &shNnz, &shLns1, &shU, &shH, &Hbuf[0], &Hbuf[1],
                          &Mb, &Wb, &Xb, &Yb, &sigb, &permb, &nnzb, &ilns1, &iflags, &lnacc, &tflags,
                          &scratch, &o_lnabs, &o_sign, &o_flags, &o_tflags, &stats, &tcXh, &tcYh, &tcXl,
-                         &tcYl, &tcScale, &tcErr, &ozExp, &Timp, &bdb, &keptb, &sigtb, &nkb, &vrowsb, &bdscr};
+                         &tcYl, &tcScale, &tcErr, &ozExp, &Timp, &bdb, &keptb, &sigtb, &nkb, &vrowsb, &bdscr,
+                         &bandb};
   size_t b = 0;
   for (const DevBuf* d : all) b += d->bytes;
   return b;
@@ -178,7 +180,8 @@ void mctrg_ctx::release_all() {
   DevBuf* all[] = {&T0, &shM, &shW, &shSig, &shPerm, &shNnz, &shLns1, &shU, &shH, &Hbuf[0], &Hbuf[1],
                    &Mb, &Wb, &Xb, &Yb, &sigb, &permb, &nnzb, &ilns1, &iflags, &lnacc, &tflags,
                    &scratch, &o_lnabs, &o_sign, &o_flags, &o_tflags, &stats, &tcXh, &tcYh, &tcXl,
-                   &tcYl, &tcScale, &tcErr, &ozExp, &Timp, &bdb, &keptb, &sigtb, &nkb, &vrowsb, &bdscr};
+                   &tcYl, &tcScale, &tcErr, &ozExp, &Timp, &bdb, &keptb, &sigtb, &nkb, &vrowsb, &bdscr,
+                   &bandb};
   for (DevBuf* b : all) b->release();
 }
 
@@ -307,9 +310,14 @@ bool route_bidiag(const mctrg_options& o, int n, int K) {
   if (o.svd == MCTRG_SVD_BIDIAG) return n >= 2;
   return n >= 64 && 2 * K >= n;
 }
+// The two-stage route replaces the one-stage one on the sizes it takes.
+bool route_band(const mctrg_options& o, int n, int K) {
+  return o.svd == MCTRG_SVD_BAND && band_supported(n) && route_bidiag(o, n, K);
+}
 }  // namespace mctrg
 
 bool mctrg_ctx::use_bidiag(int n, int K) const { return route_bidiag(opt, n, K); }
+bool mctrg_ctx::use_band(int n, int K) const { return route_band(opt, n, K); }
 
 static bool is_pow2(int L) { return L >= 2 && (L & (L - 1)) == 0; }
 
@@ -455,6 +463,8 @@ void plan_run(const std::vector<LevelInfo>& lv, int s0, int nlev, int chi, const
         const size_t ks = kept_stride(chi);
         pi += (3 * (size_t)a.n + ks + ks * (size_t)a.n) * sizeof(double) + (ks + 1) * sizeof(int);
         bd_scr = std::max(bd_scr, bd_vectors_scratch_doubles(a.n, 1 << 16, a.kc) * sizeof(double));
+        // the band route: band, panel scratch, chase reflectors, exponent
+        if (route_band(opt, a.n, (int)d2)) pi += band_item_bytes(a.n);
       }
       per_item = std::max(per_item, pi);
     }
@@ -627,6 +637,13 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
         bd_n = std::max(bd_n, (size_t)a.n);
         bd_scr = std::max(bd_scr, bd_vectors_scratch_doubles(a.n, (int)std::min<int64_t>(S, 1 << 16), a.kc));
       }
+      size_t band_n = 0;
+      for (int k = s0 + 1; k < nlev; ++k)
+        if (use_band(lv[k].n, lv[k - 1].D * lv[k - 1].D)) band_n = std::max(band_n, (size_t)lv[k].n);
+      if (band_n) {
+        CK(bandb.ensure((size_t)std::max<int64_t>(S, 1) * band_item_bytes((int)band_n) + 256));
+        CK(cudaMemsetAsync(bandb.p, 0, bandb.bytes, st));
+      }
       if (bd_n) {
         const size_t Ss = (size_t)std::max<int64_t>(S, 1);
         CK(bdb.ensure(sizeof(double) * Ss * 3 * bd_n));
@@ -668,10 +685,11 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
         CK(ozExp.ensure(sizeof(int) * 2 * oz_rows));
       }
     }
-    if (prec != MCTRG_FP64) {
+    if (prec != MCTRG_FP64 || bandb.p) {
       CK(tcErr.ensure(sizeof(uint32_t)));
       CK(cudaMemsetAsync(tcErr.p, 0, sizeof(uint32_t), st));
     }
+    uint32_t* const band_err = tcErr.as<uint32_t>();
     for (int64_t c0 = 0; c0 < n; c0 += B) {
       const int64_t Bc = std::min(B, n - c0);
       const uint64_t traj0 = first_traj + (uint64_t)c0;
@@ -798,11 +816,24 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
           sa.traj0 = traj0; sa.H = Hbuf[cur].as<double>(); sa.h_item0 = 0;
           sa.iflags = iflags.as<uint32_t>(); sa.scratch = scratch.as<double>();
           if (use_bidiag(a.n, Kd)) {
-            // bidiagonalization, bisection, choice of the kept indices, their vectors, halves
-            BidiagArgs ba{};
-            ba.M = Mb.as<double>(); ba.W = Wb.as<double>(); ba.bd = bdb.as<double>(); ba.n = a.n; ba.S = (int)Si;
-            CK(timed(MCTRG_K_BIDIAG, Si, Si * (8.0 / 3.0) * nn * nn * nn, 8.0 * Si * (2.0 * nn * nn + 3.0 * nn),
-                     [&] { return launch_bidiag(ba, st); }));
+            // bidiagonalization (one stage, or dense -> band -> bidiagonal), bisection,
+            // choice of the kept indices, their vectors, halves
+            const bool band = use_band(a.n, Kd);
+            BandArgs bda{};
+            if (band) {
+              band_carve(bandb.p, a.n, Si, bda);
+              bda.M = Mb.as<double>(); bda.Wk = (int64_t*)Wb.p; bda.bd = bdb.as<double>(); bda.S = (int)Si;
+              bda.err = band_err;
+              CK(timed(MCTRG_K_BAND, Si, Si * (8.0 / 3.0) * nn * nn * nn, 8.0 * Si * (nn * nn + 9.0 * nn),
+                       [&] { return launch_band_reduce(bda, false, st); }));
+              CK(timed(MCTRG_K_CHASE, Si, Si * 6.0 * kBandW * nn * nn, 8.0 * Si * (12.0 * nn),
+                       [&] { return launch_band_chase(bda, st); }));
+            } else {
+              BidiagArgs ba{};
+              ba.M = Mb.as<double>(); ba.W = Wb.as<double>(); ba.bd = bdb.as<double>(); ba.n = a.n; ba.S = (int)Si;
+              CK(timed(MCTRG_K_BIDIAG, Si, Si * (8.0 / 3.0) * nn * nn * nn, 8.0 * Si * (2.0 * nn * nn + 3.0 * nn),
+                       [&] { return launch_bidiag(ba, st); }));
+            }
             CK(timed(MCTRG_K_BISECT, Si, 0.0, 8.0 * Si * (3.0 * nn + a.n_pad) + 4.0 * Si * (a.n_pad + 1), [&] {
               return launch_bd_bisect(bdb.as<double>(), a.n, a.n_pad, (int)Si, sigb.as<double>(), permb.as<int>(),
                                       nnzb.as<int>(), ilns1.as<double>() + i0, zero_rel, st); }));
@@ -815,8 +846,15 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
             va.bd = bdb.as<double>(); va.R = Wb.as<double>(); va.sig = sigb.as<double>(); va.kept = keptb.as<int>();
             va.nk = nkb.as<int>(); va.vrows = vrowsb.as<double>(); va.scratch = bdscr.as<double>();
             va.n = a.n; va.n_pad = a.n_pad; va.S = (int)Si; va.kmax = a.kc; va.kstride = ks;
-            CK(timed(MCTRG_K_VECTORS, Si, Si * (2.0 * nn * nn * a.kc + 40.0 * nn * a.kc),
-                     8.0 * Si * (nn * nn / 2.0 + 3.0 * nn + 2.0 * a.kc * nn), [&] { return launch_bd_vectors(va, st); }));
+            va.skip_backtr = band ? 1 : 0;
+            CK(timed(MCTRG_K_VECTORS, Si, Si * ((band ? 4.0 : 2.0) * nn * nn * a.kc + 40.0 * nn * a.kc),
+                     8.0 * Si * (nn * nn / 2.0 + 3.0 * nn + 2.0 * a.kc * nn), [&] {
+              cudaError_t e = launch_bd_vectors(va, st);
+              if (e != cudaSuccess || !band) return e;
+              BandVecArgs bv{};
+              bv.band = &bda; bv.sig = sigb.as<double>(); bv.kept = keptb.as<int>(); bv.nk = nkb.as<int>();
+              bv.vrows = vrowsb.as<double>(); bv.n_pad = a.n_pad; bv.kstride = ks; bv.unit_rows = 0;
+              return launch_band_backtr(bv, st); }));
             sa.mode = 2; sa.vrows = vrowsb.as<double>();
             CK(timed(MCTRG_K_SAMPLE, Si, Si * 2.0 * nn * nn * a.kc, 8.0 * Si * (2.0 * nn * nn + 2.0 * nn * a.kc),
                      [&] { return launch_sample_split(sa, st, grid_s); }));
@@ -866,7 +904,7 @@ int mctrg_ctx::run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs_
   if (sign_out) CK(cudaMemcpyAsync(sign_out, o_sign.p, (size_t)n, cudaMemcpyDefault, st));
   if (flags_out) CK(cudaMemcpyAsync(flags_out, o_flags.p, (size_t)n, cudaMemcpyDefault, st));
   uint32_t tc_err = 0;
-  if (opt.precision != MCTRG_FP64 && tcErr.p)
+  if ((opt.precision != MCTRG_FP64 || opt.svd == MCTRG_SVD_BAND) && tcErr.p)
     CK(cudaMemcpyAsync(&tc_err, tcErr.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   resolve_events();

@@ -32,6 +32,7 @@ struct LevelInfo {
 };
 
 bool route_bidiag(const mctrg_options& o, int n, int K);
+bool route_band(const mctrg_options& o, int n, int K);
 void plan_run(const std::vector<LevelInfo>& lv, int s0, int nlev, int chi, const mctrg_options& opt,
               size_t budget, int64_t n_samples, int64_t& B, int64_t& S, size_t& total);
 void plan_run_bound(int L, int chi, int D0, const mctrg_options& opt, size_t budget, int64_t n_samples,
@@ -66,6 +67,7 @@ struct mctrg_ctx {
   mctrg::DevBuf ozExp;                                     // FP64TC: row exponents of X and Yt
   mctrg::DevBuf Timp;                                      // impurity tensor (level0_distinct)
   mctrg::DevBuf bdb, keptb, sigtb, nkb, vrowsb, bdscr;    // bidiagonalization route
+  mctrg::DevBuf bandb;                                     // band route: band, scratch, reflectors
 
   // per-kernel-class statistics (MCTRG_K_*)
   mctrg_kernel_stat kstat[MCTRG_K_COUNT]{};
@@ -99,6 +101,7 @@ struct mctrg_ctx {
 
   int init_from_device_tensor(int D0, int L, int chi);
   bool use_bidiag(int n, int K) const;
+  bool use_band(int n, int K) const;
   void plan_chunks(int64_t n_samples, int64_t& B, int64_t& S, size_t& total) const;
   int run(int64_t n, uint64_t seed, uint64_t first_traj, double* lnabs, int8_t* sign, uint8_t* flags,
           mctrg_estimate* est);

@@ -1,11 +1,12 @@
-// C-ABI access to the batched SVD (K2) on its own: the Jacobi route and the
-// bidiagonalization route.
+// C-ABI access to the batched SVD (K2) on its own: the Jacobi route, the
+// bidiagonalization route and the two-stage (band) route.
 #include <algorithm>
 #include <vector>
 
 #include "../../include/mctrg.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "kernels_band.h"
 #include "kernels_bd.h"
 #include "mctrg_internal.h"
 
@@ -104,6 +105,110 @@ extern "C" int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, d
     if (e != cudaSuccess) { status = MCTRG_ECUDA; break; }
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) status = MCTRG_ECUDA;
+  cudaFree(buf);
+  return status;
+}
+
+// Device buffers of the band route for `chunk` matrices of side n, carved
+// from one allocation: Wk (n x n), bd (3n), then band_carve's.
+static size_t band_bytes(int n, int64_t chunk) {
+  // rounded up to 256 bytes: the buffers that follow hold doubles
+  const size_t b = (size_t)chunk * (sizeof(double) * ((size_t)n * n + 3 * (size_t)n) + band_item_bytes(n)) + 256;
+  return (b + 255) & ~(size_t)255;
+}
+static void band_all(void* buf, int n, int64_t chunk, BandArgs& a) {
+  double* p = (double*)buf;
+  a.Wk = (int64_t*)p; p += (size_t)chunk * n * n;
+  a.bd = p; p += (size_t)chunk * 3 * n;
+  band_carve(p, n, chunk, a);
+}
+
+extern "C" int mctrg_band_reduce_batched(const double* M, int n, int64_t batch, double* band, double* bd,
+                                         void* stream) {
+  if (!M || !band || !band_supported(n) || batch < 1 || batch > (1 << 30)) return MCTRG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return MCTRG_ECUDA;
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>({batch, (int64_t)(fr / 4 / band_bytes(n, 1)), 1 << 14}));
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, band_bytes(n, chunk)) != cudaSuccess) return MCTRG_ENOMEM;
+  BandArgs a{};
+  band_all(buf, n, chunk, a);
+  int status = cudaMemsetAsync(a.err, 0, sizeof(uint32_t), st) == cudaSuccess ? MCTRG_OK : MCTRG_ECUDA;
+  for (int64_t b0 = 0; b0 < batch && status == MCTRG_OK; b0 += chunk) {
+    const int cnt = (int)std::min(chunk, batch - b0);
+    a.M = M + (size_t)b0 * n * n; a.S = cnt;
+    cudaError_t e = launch_band_reduce(a, bd != nullptr, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(band + (size_t)b0 * n * (kBandW + 1), a.band, sizeof(double) * cnt * n * (kBandW + 1),
+                          cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && bd)
+      e = cudaMemcpyAsync(bd + (size_t)b0 * 3 * n, a.bd, sizeof(double) * cnt * 3 * n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) status = MCTRG_ECUDA;
+  }
+  uint32_t err = 0;
+  if (cudaMemcpyAsync(&err, a.err, sizeof(err), cudaMemcpyDeviceToHost, st) != cudaSuccess) status = MCTRG_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) status = MCTRG_ECUDA;
+  if (status == MCTRG_OK && err) status = MCTRG_ECUDA;
+  cudaFree(buf);
+  return status;
+}
+
+extern "C" int mctrg_svd_band_batched(const double* M, int n, int64_t batch, double* sigma, int n_vec,
+                                      double* vt, void* stream) {
+  if (!M || !sigma || !band_supported(n) || batch < 1 || batch > (1 << 30)) return MCTRG_EINVAL;
+  if (n_vec < 0 || n_vec > 16 || n_vec > n || (n_vec > 0 && !vt)) return MCTRG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int np = n + (n & 1);
+  const int ks = kept_stride(n_vec);
+  const size_t per_extra = ((size_t)np + (size_t)ks * n) * sizeof(double) + ((size_t)np + 1 + ks + 1) * sizeof(int);
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return MCTRG_ECUDA;
+  const int64_t chunk = std::max<int64_t>(
+      1, std::min<int64_t>({batch, (int64_t)(fr / 4 / (band_bytes(n, 1) + per_extra)), 1 << 14}));
+  const size_t scr = bd_vectors_scratch_doubles(n, (int)chunk, std::max(1, n_vec)) * sizeof(double);
+  const size_t bb = band_bytes(n, chunk);
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, bb + per_extra * (size_t)chunk + scr) != cudaSuccess) return MCTRG_ENOMEM;
+  BandArgs a{};
+  band_all(buf, n, chunk, a);
+  double* sig = (double*)((char*)buf + bb);
+  double* vrows = sig + (size_t)chunk * np;
+  double* scratch = vrows + (size_t)chunk * ks * n;
+  int* perm = (int*)(scratch + scr / sizeof(double));
+  int* nnz = perm + (size_t)chunk * np;
+  int* kept = nnz + chunk;
+  int* nk = kept + (size_t)chunk * ks;
+  int status = cudaMemsetAsync(a.err, 0, sizeof(uint32_t), st) == cudaSuccess ? MCTRG_OK : MCTRG_ECUDA;
+  for (int64_t b0 = 0; b0 < batch && status == MCTRG_OK; b0 += chunk) {
+    const int cnt = (int)std::min(chunk, batch - b0);
+    a.M = M + (size_t)b0 * n * n; a.S = cnt;
+    cudaError_t e = launch_band_reduce(a, true, st);
+    if (e == cudaSuccess) e = launch_bd_bisect(a.bd, n, np, cnt, sig, perm, nnz, nullptr, 0.0, st);
+    if (e == cudaSuccess && n_vec > 0) {
+      k_kept_leading<<<(cnt + 127) / 128, 128, 0, st>>>(kept, nk, nnz, n_vec, cnt, ks);
+      BdVecArgs va{};
+      va.bd = a.bd; va.R = nullptr; va.sig = sig; va.kept = kept; va.nk = nk; va.vrows = vrows; va.scratch = scratch;
+      va.n = n; va.n_pad = np; va.S = cnt; va.unit_rows = 1; va.kmax = n_vec; va.kstride = ks; va.skip_backtr = 1;
+      e = launch_bd_vectors(va, st);
+      if (e == cudaSuccess) {
+        BandVecArgs bv{};
+        bv.band = &a; bv.sig = sig; bv.kept = kept; bv.nk = nk; bv.vrows = vrows; bv.n_pad = np; bv.kstride = ks;
+        bv.unit_rows = 1;
+        e = launch_band_backtr(bv, st);
+      }
+    }
+    if (e == cudaSuccess) {
+      k_bd_finalize<<<cnt, 256, 0, st>>>(sig, n, np, n_vec, vrows, sigma + (size_t)b0 * n,
+                                          n_vec > 0 ? vt + (size_t)b0 * n_vec * n : nullptr, ks);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) status = MCTRG_ECUDA;
+  }
+  uint32_t err = 0;
+  if (cudaMemcpyAsync(&err, a.err, sizeof(err), cudaMemcpyDeviceToHost, st) != cudaSuccess) status = MCTRG_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) status = MCTRG_ECUDA;
+  if (status == MCTRG_OK && err) status = MCTRG_ECUDA;
   cudaFree(buf);
   return status;
 }

@@ -25,11 +25,13 @@ EXPORTS = [
     "mctrg_reset_kernel_stats", "mctrg_svd_batched", "mctrg_svd_batched_noalloc",
     "mctrg_svd_bidiag_batched", "mctrg_measure_fp64_peak", "mctrg_contract_batched",
     "mctrg_server_footprint", "mctrg_server_memory", "mctrg_batch_run", "mctrg_init_impurity",
-    "mctrg_ratio_estimate", "mctrg_hotrg_run",
+    "mctrg_ratio_estimate", "mctrg_hotrg_run", "mctrg_svd_band_batched", "mctrg_band_reduce_batched",
 ]
-K_FORM_XY, K_GEMM, K_JACOBI, K_SAMPLE, K_TRACE, K_OTHER, K_BIDIAG, K_BISECT, K_VECTORS, K_COUNT = range(10)
-KERNEL_NAMES = ["form_xy", "gemm", "jacobi", "sample_split", "trace", "other", "bidiag", "bisect", "vectors"]
-SVD_AUTO, SVD_JACOBI, SVD_BIDIAG = 0, 1, 2
+(K_FORM_XY, K_GEMM, K_JACOBI, K_SAMPLE, K_TRACE, K_OTHER, K_BIDIAG, K_BISECT, K_VECTORS, K_BAND, K_CHASE,
+ K_COUNT) = range(12)
+KERNEL_NAMES = ["form_xy", "gemm", "jacobi", "sample_split", "trace", "other", "bidiag", "bisect", "vectors", "band",
+                "chase"]
+SVD_AUTO, SVD_JACOBI, SVD_BIDIAG, SVD_BAND = 0, 1, 2, 3
 
 
 class KernelStat(ctypes.Structure):
@@ -108,6 +110,8 @@ def lib():
             "mctrg_svd_batched": (c_int, [vp, c_int, i64, vp, vp, c_int, vp]),
             "mctrg_svd_batched_noalloc": (c_int, [vp, c_int, i64, vp, vp, c_int, vp]),
             "mctrg_svd_bidiag_batched": (c_int, [vp, c_int, i64, vp, c_int, vp, vp]),
+            "mctrg_svd_band_batched": (c_int, [vp, c_int, i64, vp, c_int, vp, vp]),
+            "mctrg_band_reduce_batched": (c_int, [vp, c_int, i64, vp, vp, vp]),
             "mctrg_measure_fp64_peak": (c_int, [c_int, i64, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
             "mctrg_contract_batched": (c_int, [vp, vp, c_int, c_int, i64, vp, c_int, vp]),
         }
@@ -275,6 +279,23 @@ def mctrg_svd_bidiag_batched(M, sigma, vt=None, stream=None):
     batch, n = int(M.shape[0]), int(M.shape[-1])
     nv = 0 if vt is None else int(vt.shape[1])
     return lib().mctrg_svd_bidiag_batched(_ptr(M), n, batch, _ptr(sigma), nv, _ptr(vt), stream)
+
+
+def mctrg_svd_band_batched(M, sigma, vt=None, stream=None):
+    """Two-stage (band) route: M (batch, n, n) float64 device tensor, n a
+    multiple of 8 from 64 to 256; sigma (batch, n); vt (batch, n_vec, n),
+    n_vec <= 16, receives the unit right vectors of the n_vec largest singular
+    values (None: values only)."""
+    batch, n = int(M.shape[0]), int(M.shape[-1])
+    nv = 0 if vt is None else int(vt.shape[1])
+    return lib().mctrg_svd_band_batched(_ptr(M), n, batch, _ptr(sigma), nv, _ptr(vt), stream)
+
+
+def mctrg_band_reduce_batched(M, band, bd=None, stream=None):
+    """Stage 1 (and 2 when bd is given) of the band route: band (batch, n, 9)
+    receives B(i, i+o); bd (batch, 3n) the bidiagonal's d, e."""
+    batch, n = int(M.shape[0]), int(M.shape[-1])
+    return lib().mctrg_band_reduce_batched(_ptr(M), n, batch, _ptr(band), _ptr(bd), stream)
 
 
 def mctrg_batch_run(jobs, opts=None, lnabsZ=None, sign=None, flags=None):

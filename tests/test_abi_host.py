@@ -107,7 +107,7 @@ def test_create_rejects_bad_options_before_touching_the_device():
     import ctypes
     lib = mctrg.lib()
     h = ctypes.c_void_p()
-    for bad in (dict(precision=9), dict(svd=3), dict(svd=-1), dict(zero_tol_scale=-1.0),
+    for bad in (dict(precision=9), dict(svd=4), dict(svd=-1), dict(zero_tol_scale=-1.0),
                 dict(zero_tol_scale=float("inf")), dict(zero_tol_scale=float("nan")),
                 dict(deterministic_levels=-1)):
         o = mctrg.make_options(**bad)
