@@ -144,10 +144,10 @@ def oracle_rate(wl, seconds_budget=20.0, workers=None):
 SERVE_MAX_SAMPLES = 1 << 16
 
 
-def _serve_mix(rng):
+def _serve_mix(rng, max_samples=SERVE_MAX_SAMPLES):
     """One job of the serving stand-in (small lattices; the literal sizes run as refusals)."""
     return (float(rng.uniform(0.3, 0.6)), float(rng.choice([0.0, 0.05])), int(rng.choice([4, 8, 16, 32])),
-            int(rng.choice([2, 4, 8])), float(10 ** rng.uniform(-4, -2)), SERVE_MAX_SAMPLES, int(rng.integers(1 << 62)))
+            int(rng.choice([2, 4, 8])), float(10 ** rng.uniform(-4, -2)), int(max_samples), int(rng.integers(1 << 62)))
 
 
 def _serve_literal(rng):
@@ -157,19 +157,27 @@ def _serve_literal(rng):
             int(rng.choice([8, 16, 32])), float(10 ** rng.uniform(-6, -4)), 1 << 18, int(rng.integers(1 << 62)))
 
 
-def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_every=3, drain_s=120.0, burst_jobs=16):
-    """Continuous batching under Poisson arrivals at a stated fraction of capacity.
+SERVE_ARRIVALS_PER_S = 200.0
+
+
+def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_jobs=3, drain_s=120.0, burst_jobs=16):
+    """Continuous batching under Poisson arrivals at 200 requests/s, job sizes scaled to a
+    stated fraction of capacity.
 
     Job mix (small-lattice stand-in of the serving workload): beta uniform in
     [0.3, 0.6], h in {0, 0.05}, L in {4, 8, 16, 32}, chi in {2, 4, 8}, target
-    standard error of ln Z log-uniform in [1e-4, 1e-2], at most 2^16
-    trajectories; every `literal_every`-th arrival is a job at the literal
-    sizes, which must be refused at submission (footprint beyond the device)
-    or stopped after its first round (target projected out of reach).  The
-    server's capacity (trajectories/s and trajectories per job) is measured
-    first on a burst of `burst_jobs` jobs from the mix; arrivals then come at `load`
-    times the job rate that capacity sustains.  Jobs still running `drain_s`
-    after the last arrival are reported as unfinished.
+    standard error of ln Z log-uniform in [1e-4, 1e-2].  After the arrivals,
+    `literal_jobs` jobs at the literal sizes are submitted; each must be refused at
+    submission (footprint beyond the device) or stopped after its first round
+    (target projected out of reach), and their latency is reported apart (a first
+    round at these sizes holds a worker for seconds, which would swamp the mix's
+    percentiles if they arrived with it).  The server's trajectory capacity is measured on a
+    burst of `burst_jobs` jobs of the mix (at most 2^16 trajectories each); the
+    job size is then scaled, through each job's sample cap, so that 200 jobs/s
+    offer `load` times that capacity, and the server's job rate at that size is
+    measured on a second burst (arrivals slow to `load` times it if it cannot take
+    200/s).  Jobs still running `drain_s` after the last arrival are reported as
+    unfinished.
     """
     import numpy as np
     rng = np.random.default_rng(seed)
@@ -179,7 +187,13 @@ def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_every=3, 
         burst = [mctrg.mctrg_server_submit(srv, *_serve_mix(rng))[1] for _ in range(burst_jobs)]
         traj = sum(mctrg.mctrg_server_wait(srv, j, 900.0)[1].n for j in burst)
         cap = traj / (time.perf_counter() - t0)
-        rate = load * cap / (traj / float(burst_jobs))
+        cap_samples = int(min(SERVE_MAX_SAMPLES, max(4, round(load * cap / SERVE_ARRIVALS_PER_S))))
+        t0 = time.perf_counter()
+        burst = [mctrg.mctrg_server_submit(srv, *_serve_mix(rng, cap_samples))[1] for _ in range(8 * burst_jobs)]
+        for j in burst:
+            mctrg.mctrg_server_wait(srv, j, 900.0)
+        job_cap = 8 * burst_jobs / (time.perf_counter() - t0)
+        rate = min(SERVE_ARRIVALS_PER_S, load * job_cap)
         ids, lit, refused, n_arr = [], [], 0, 0
         t0 = time.perf_counter()
         t_next = 0.0
@@ -188,17 +202,9 @@ def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_every=3, 
             if now < t_next:
                 time.sleep(t_next - now)
             n_arr += 1
-            if literal_every and n_arr % literal_every == 0:
-                ts = time.perf_counter()
-                st, j = mctrg.mctrg_server_submit(srv, *_serve_literal(rng))
-                if st == 0:
-                    lit.append((j, ts))
-                else:
-                    refused += 1
-            else:
-                st, j = mctrg.mctrg_server_submit(srv, *_serve_mix(rng))
-                if st == 0:
-                    ids.append(j)
+            st, j = mctrg.mctrg_server_submit(srv, *_serve_mix(rng, cap_samples))
+            if st == 0:
+                ids.append(j)
             t_next += float(rng.exponential(1.0 / rate))
         t_end = time.perf_counter()
         lat, n_traj, reached, projected, unfinished = [], 0, 0, 0, 0
@@ -211,25 +217,38 @@ def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_every=3, 
             n_traj += est.n
             reached += st == 0
             projected += st == mctrg.MCTRG_EUNREACHABLE
-        lit_lat = []
-        for j, ts in lit:
-            st, est, l = mctrg.mctrg_server_wait(srv, j, 600.0)
-            lit_lat.append(l)
         wall = time.perf_counter() - t0
+        lit_lat, lit_sizes = [], []
+        for _ in range(literal_jobs):
+            job = _serve_literal(rng)
+            lit_sizes.append("L=%d chi=%d" % (job[2], job[3]))
+            ts = time.perf_counter()
+            st, j = mctrg.mctrg_server_submit(srv, *job)
+            if st != 0:
+                refused += 1
+                lit_lat.append(time.perf_counter() - ts)
+                continue
+            st, est, l = mctrg.mctrg_server_wait(srv, j, 600.0)
+            lit.append(st)
+            lit_lat.append(l)
     finally:
         mctrg.mctrg_server_destroy(srv)
     lat = np.sort(np.array(lat))
-    return {"capacity_trajectories_per_s": cap, "offered_load": load, "offered_jobs_per_s": rate,
+    return {"capacity_trajectories_per_s": cap, "offered_load": load, "arrivals_per_s": rate,
+            "sample_cap_per_job": cap_samples, "job_capacity_per_s": job_cap,
             "jobs": len(ids), "seconds_of_arrivals": seconds,
             "latency_p50_s": float(lat[len(lat) // 2]) if len(lat) else None,
             "latency_p99_s": float(lat[min(len(lat) - 1, int(0.99 * len(lat)))]) if len(lat) else None,
             "trajectories_per_s": n_traj / wall, "jobs_reaching_target": reached,
             "jobs_projected_unreachable": projected, "jobs_unfinished_after_drain": unfinished,
-            "literal_jobs": {"refused_at_submit": refused, "projected_out_of_reach": len(lit),
-                             "latency_max_s": max(lit_lat) if lit_lat else None},
+            "literal_jobs": {"sizes": lit_sizes, "refused_at_submit": refused,
+                             "projected_out_of_reach": int(sum(1 for x in lit if x == mctrg.MCTRG_EUNREACHABLE)),
+                             "other_status": [int(x) for x in lit if x != mctrg.MCTRG_EUNREACHABLE],
+                             "latency_s": lit_lat},
             "mix": "beta U[0.3,0.6], h {0,0.05}, L {4,8,16,32}, chi {2,4,8}, target SE(ln Z) 1e-4..1e-2 "
-                   "log-uniform, max 2^16 trajectories; every %dth arrival at the literal sizes (L 2^8..2^16, "
-                   "chi {8,16,32}, target 1e-6..1e-4)" % literal_every}
+                   "log-uniform; job size scaled by the per-job sample cap so that the arrival rate offers "
+                   "%.0f%% of the measured trajectory capacity; then %d jobs at the literal sizes "
+                   "(L 2^8..2^16, chi {8,16,32}, target 1e-6..1e-4)" % (100 * load, literal_jobs)}
 
 
 def _uneven_jobs(n_jobs, seed):

@@ -157,20 +157,21 @@ __device__ __forceinline__ void store_slices(uint8_t* tiles, uint32_t tile_bytes
   }
 }
 
-__device__ __forceinline__ uint64_t slice_desc(const uint8_t* tiles, uint32_t tile_bytes, int q, int s) {
-  return umma_desc(smem_u32(tiles + (size_t)(q * 2 + (s >> 2)) * tile_bytes) + (uint32_t)((s & 3) * 32));
-}
-
-// The 36 products of a k-step: accumulator g = i + j at columns g * N.
+// The 36 products of a k-step: accumulator g = i + j at columns g * N.  Two
+// descriptors are formed per call; each product's start addresses differ from
+// them by compile-time offsets (the 14-bit start field holds address / 16).
 __device__ __forceinline__ void issue_products(uint32_t tmem, const uint8_t* A, uint32_t abytes, const uint8_t* Bt,
                                                uint32_t bbytes, int q, int N, uint32_t idesc, bool first) {
+  const uint64_t a0 = umma_desc(smem_u32(A + (size_t)q * 2 * abytes));
+  const uint64_t b0 = umma_desc(smem_u32(Bt + (size_t)q * 2 * bbytes));
 #pragma unroll
   for (int g = 0; g < kSl; ++g)
 #pragma unroll
     for (int i = 0; i <= g; ++i) {
       const int j = g - i;
-      umma<1>(tmem + (uint32_t)(g * N), slice_desc(A, abytes, q, i), slice_desc(Bt, bbytes, q, j), idesc,
-              (first && i == 0) ? 0u : 1u);
+      const uint64_t ad = a0 + (uint64_t)((((i >> 2) * abytes) + (i & 3) * 32) >> 4);
+      const uint64_t bd = b0 + (uint64_t)((((j >> 2) * bbytes) + (j & 3) * 32) >> 4);
+      umma<1>(tmem + (uint32_t)(g * N), ad, bd, idesc, (first && i == 0) ? 0u : 1u);
     }
 }
 
@@ -746,12 +747,15 @@ __global__ void __launch_bounds__(256) k_band_gemm_x(BandArgs a, int k) {
 // Trailing update A[k+b:][k+b:] -= [V | Y] [Z ; U] for one 128-row tile, its
 // 32-column tiles in turn: K = 2b = 16 (one k-step), applied in fixed point.
 // The operands are [V 2^eA | Y] and [Z 2^-eA ; U] (the same product): V and U
-// are of order 1, Y and Z of order |A|, and each operand row or column shares
-// one exponent.  256 threads: the row operand is split once (V halves by
-// threads 0-127, Y halves by 128-255); per column tile two warps split the
-// column operand, thread 0 issues the 36 products, and warp w applies the
-// results of rows 32 (w % 4) .. +31 (its tensor-memory lanes) and columns
-// 16 (w / 4) .. +15 of the tile, all loads of a row segment issued together.
+// are of order 1, Y and Z of order |A|.  The row operand shares one exponent
+// over the tile's rows, the column operand one over each 32-column tile (both
+// the largest of the per-row / per-column exponents: digits keep 62 bits of
+// the largest entry), so every element of a tile takes the same shifts.  256
+// threads: the row operand is split once (V halves by threads 0-127, Y halves
+// by 128-255); per column tile two warps split the column operand, thread 0
+// issues the 36 products, and warp w applies the results of rows 32 (w % 4)
+// .. +31 (its tensor-memory lanes) and columns 16 (w / 4) .. +15 of the tile,
+// the row segment loaded before the products run.
 __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* As = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -760,9 +764,7 @@ __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
   uint8_t* Bs = As + 2 * kTileBytes;
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_fail;
-  __shared__ int ers[N];
-  __shared__ int els[kTileM];
+  __shared__ int s_fail, s_el, s_er;
   const int s = blockIdx.x, n = a.n, t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int r0 = k + B + blockIdx.y * kTileM;       // first row of the tile
   long long* A = (long long*)a.Wk + (size_t)s * n * n;
@@ -771,17 +773,27 @@ __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
   const int eA = a.eA[s];
   if (t == 0) {
     s_fail = 0;
+    s_el = kZeroExp;
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(&tmem_slot, 256);
+  __syncthreads();
   {
-    // A operand: row rho = [V[r] 2^eA | Y[r]] with the row exponent el
+    // the tile's row exponent: the largest el of its rows
+    const int r = r0 + (t & 127);
+    int e = (t < 128 && r < n) ? w.el[r - k - B] : kZeroExp;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (lane == 0 && t < 128) atomicMax(&s_el, e);
+  }
+  __syncthreads();
+  const int el = s_el;
+  {
+    // A operand: row rho = [V[r] 2^eA | Y[r]]
     const int rho = t & 127, part = t >> 7, r = r0 + rho;
     long long x[8];
-    int el = kZeroExp;
-    if (r < n) {
-      el = w.el[r - k - B];
+    if (r < n && el != kZeroExp) {
 #pragma unroll
       for (int e = 0; e < 8; ++e)
         x[e] = part == 0 ? fix_of(w.V[(size_t)(r - k) * 8 + e], kFloatP - el + eA)
@@ -790,7 +802,6 @@ __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
 #pragma unroll
       for (int e = 0; e < 8; ++e) x[e] = 0;
     }
-    if (part == 0) els[rho] = el;
     uint4 d[kSl];
     digits8(x, d);
     store_slices(As, kTileBytes, 0, part, rho, d);
@@ -802,7 +813,6 @@ __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
   const uint32_t idesc = umma_idesc(1, kTileM, N);
   const int quad = warp & 3, hc = warp >> 2;
   const int rho = quad * 32 + lane, r = r0 + rho;
-  const int el = els[rho];
   const int ntile = (n - k - B + N - 1) / N;
   for (int ct = 0; ct < ntile; ++ct) {
     const int cb = k + B + ct * N;                  // first column of the tile
@@ -817,10 +827,12 @@ __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
     }
     if (t < 2 * N) {                                 // B operand: column c = [Z[:, c] 2^-eA ; U[:, c]]
       const int cc = t & (N - 1), part = t >> 5, c = cb + cc;
+      int er = c < n ? w.er[c - k - B] : kZeroExp;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) er = max(er, __shfl_xor_sync(0xffffffffu, er, o));
+      if (t == 0) s_er = er;                         // the tile's column exponent
       long long x[8];
-      int er = kZeroExp;
-      if (c < n) {
-        er = w.er[c - k - B];
+      if (c < n && er != kZeroExp) {
 #pragma unroll
         for (int e = 0; e < 8; ++e)
           x[e] = part == 0 ? fix_of(w.Z[(size_t)e * n + (c - k - B)], kFloatP - er - eA)
@@ -829,7 +841,6 @@ __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) x[e] = 0;
       }
-      if (part == 0) ers[cc] = er;
       uint4 d[kSl];
       digits8(x, d);
       store_slices(Bs, bt, 0, part, cc, d);
@@ -846,43 +857,57 @@ __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
     tc_fence_after();
     __syncthreads();
     if (s_fail) break;
+    const int er = s_er;
+    // value of an element: (hi 2^32 + lo) 2^(el + er - 68), in fixed-point
+    // units 2^(eA - 59): shifted by sh = el + er - eA - 9, the same for the
+    // whole tile.  The tensor-memory loads are warp-collective: every lane
+    // issues them; only the arithmetic and the stores depend on the row.
+    const bool apply = rowok && er != kZeroExp;
+    const int sh = el + er - eA - 9;
 #pragma unroll
     for (int part = 0; part < 2; ++part) {           // this warp's 16 columns, 8 at a time
       const int jc = hc * NH + part * 8;
       // group sums here are integers of at most 8 x 16 x 2^14 = 2^21 in
-      // magnitude: read back exactly by adding 1.5 2^23 (an FP32 add and an
-      // integer subtract)
-      long long hi[8], lo[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) { hi[j] = 0; lo[j] = 0; }
+      // magnitude, read back exactly by adding 1.5 2^23 (an FP32 add; the
+      // bias 0x4B400000 of each is taken out of the pair sums below) and
+      // paired in 32 bits: G0 2^8 + G1 and so on stay below 2^30
+      int gb[kSl][8];
 #pragma unroll
       for (int g = 0; g < kSl; ++g) {
         uint32_t v[8];
         tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * N + jc), v);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const long long G = (long long)(__float_as_int(__uint_as_float(v[j]) + 12582912.0f) - 0x4B400000);
-          if (g < 4) hi[j] = (hi[j] << 8) + G;
-          else lo[j] = (lo[j] << 8) + G;
-        }
+        for (int j = 0; j < 8; ++j) gb[g][j] = __float_as_int(__uint_as_float(v[j]) + 12582912.0f);
       }
-      if (rowok) {
+      if (apply) {
+        // (b 2^8 + b) of two biased sums, modulo 2^32 (the pairs are exact in
+        // 32-bit two's complement)
+        constexpr uint32_t kBias = 0x4B400000u * 257u;
+        auto pair = [&](int g, int j) {
+          return (int)((uint32_t)gb[g][j] * 256u + (uint32_t)gb[g + 1][j] - kBias);
+        };
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int j = 2 * i;
-          const int e0 = ers[jc + j], e1 = ers[jc + j + 1];
-          longlong2& qq = q[part * 4 + i];
-          if (e0 != kZeroExp)
-            qq.x -= shift_round(hi[j], 32 + el + e0 - eA - 9) + shift_round(lo[j], el + e0 - eA - 9);
-          if (e1 != kZeroExp)
-            qq.y -= shift_round(hi[j + 1], 32 + el + e1 - eA - 9) + shift_round(lo[j + 1], el + e1 - eA - 9);
-        }
+          long long del[2];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) rowp[part * 4 + i] = q[part * 4 + i];
+          for (int h = 0; h < 2; ++h) {
+            const int j = 2 * i + h;
+            const int h01 = pair(0, j), h23 = pair(2, j), l45 = pair(4, j), l67 = pair(6, j);
+            const long long hi = (long long)h01 * 65536 + h23, lo = (long long)l45 * 65536 + l67;
+            del[h] = shift_round(hi, 32 + sh) + shift_round(lo, sh);
+          }
+          longlong2& qq = q[part * 4 + i];
+          qq.x -= del[0];
+          qq.y -= del[1];
+        }
       }
     }
+    if (apply) {
+#pragma unroll
+      for (int i = 0; i < NH / 2; ++i) rowp[i] = q[i];
+    }
     tc_fence_before();
-    __syncthreads();                                 // ers and the B tiles are rewritten next
+    __syncthreads();                                 // s_er and the B tiles are rewritten next
   }
   if (s_fail && t == 0) atomicOr(a.err, 1u);
   tc_fence_before();

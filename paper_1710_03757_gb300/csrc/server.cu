@@ -223,6 +223,30 @@ extern "C" int mctrg_server_create(const mctrg_options* opt, mctrg_server_t* out
   return MCTRG_OK;
 }
 
+// Trajectories of a job's first round: about 0.5 s of SVD work, at least 2
+// (a standard error needs two) and at most 256, so that a job whose target is
+// out of reach is projected so after one short round whatever its lattice.
+// The work is the bidiagonal reduction's n^3 per matrix summed over the levels
+// that each trajectory splits on its own (after the first sampled level, which
+// is shared), with the Ising site tensor's bond dimensions (D_1 = 2: the level-0
+// matrix has rank 2; then D' = min(chi, D^2)), at about 5e11 n^3 per second
+// (measured on the 1024 x 1024, chi = 16 lattice).
+static int64_t first_round(int L, int chi) {
+  int m = 0;
+  while ((1 << m) < L) ++m;
+  double work = 0.0;
+  int D = 2;
+  bool sampled = false;
+  for (int k = 0; k < 2 * m; ++k) {
+    const double n = (double)D * D;
+    if (sampled) work += (double)(((int64_t)L * L) >> k) * n * n * n;
+    if (n > chi) sampled = true;
+    D = k == 0 ? 2 : std::min(chi, D * D);
+  }
+  if (work <= 0.0) return 256;
+  return std::max<int64_t>(2, std::min<int64_t>(256, (int64_t)(2.5e11 / work)));
+}
+
 extern "C" int mctrg_server_submit(mctrg_server_t s, double beta, double h, int L, int chi,
                                    double target_se_lnZ, int64_t max_samples, uint64_t seed,
                                    uint64_t* job_id) {
@@ -234,7 +258,7 @@ extern "C" int mctrg_server_submit(mctrg_server_t s, double beta, double h, int 
   Job* j = new Job();
   j->beta = beta; j->h = h; j->L = L; j->chi = chi; j->target = target_se_lnZ;
   j->max_samples = max_samples; j->seed = seed;
-  j->round0 = L <= 64 ? 256 : (L <= 256 ? 32 : 4);
+  j->round0 = first_round(L, chi);
   // footprint of the largest round within half the budget (so that other jobs
   // run beside it); a job of which not even one trajectory fits the whole
   // budget can never run

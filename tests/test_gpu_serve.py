@@ -95,9 +95,10 @@ def test_status_codes():
         assert mctrg.mctrg_server_poll(srv, j)[0] == mctrg.MCTRG_EAGAIN
         assert mctrg.mctrg_server_wait(srv, j, 0.01)[0] == mctrg.MCTRG_ETIMEDOUT
         # a target that max_samples cannot reach: projected after the first
-        # round (256 trajectories), result returned, status says so
+        # round (about half a second of work, 2 to 256 trajectories), result
+        # returned, status says so
         st, est, lat = mctrg.mctrg_server_wait(srv, j, 300.0)
-        assert st == mctrg.MCTRG_EUNREACHABLE and est.n == 256
+        assert st == mctrg.MCTRG_EUNREACHABLE and 2 <= est.n <= 256
         # destroying the server with a job still running is clean
         st, j2 = mctrg.mctrg_server_submit(srv, 0.44, 0.0, 32, 16, 1e-9, 1 << 14, 4)
         assert st == 0
@@ -168,7 +169,8 @@ def test_literal_configurations_are_refused_fast():
                for L, chi, tgt in ((256, 8, 1e-5), (512, 8, 1e-6), (256, 16, 1e-6))]
         for j in ids:
             st, est, lat = mctrg.mctrg_server_wait(srv, j, 600.0)
-            assert st == mctrg.MCTRG_EUNREACHABLE and est.n <= 32
+            # one first round: about half a second of work, at most 256 trajectories
+            assert st == mctrg.MCTRG_EUNREACHABLE and est.n <= 64
         print("literal jobs refused or projected out of reach in %.1f s" % (time.time() - t))
     finally:
         mctrg.mctrg_server_destroy(srv)
