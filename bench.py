@@ -251,6 +251,27 @@ def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_jobs=3, d
                    "(L 2^8..2^16, chi {8,16,32}, target 1e-6..1e-4)" % (100 * load, literal_jobs)}
 
 
+def svd_bench(mctrg, torch, S, n=256, nv=16):
+    """The band route (tensor-core dense -> band reduction) and the one-stage
+    bidiagonalization route on the same S random n x n matrices, values and nv
+    kept vectors: one untimed call, then one call each timed with CUDA events."""
+    g = torch.Generator(device="cuda").manual_seed(0x5FD)
+    A = torch.randn((S, n, n), dtype=torch.float64, device="cuda", generator=g)
+    sig = torch.zeros((S, n), dtype=torch.float64, device="cuda")
+    vt = torch.zeros((S, nv, n), dtype=torch.float64, device="cuda")
+    out = {"matrices": S, "n": n, "kept_vectors": nv}
+    for name, fn in (("band", mctrg.mctrg_svd_band_batched), ("bidiag", mctrg.mctrg_svd_bidiag_batched)):
+        st = fn(A, sig, vt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = fn(A, sig, vt)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"status": st, "ms": e0.elapsed_time(e1)}
+    return out
+
+
 def _uneven_jobs(n_jobs, seed):
     """The uneven-batch stand-in: chi in {4, 8, 16, 24}, L in {8, 16, 32, 64} (L <= 32 for
     chi > 8), beta uniform in [0.3, 0.6], h uniform in [0, 0.1], 64-512 trajectories each."""
@@ -447,6 +468,9 @@ def main():
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-time-to-se", action="store_true")
     ap.add_argument("--no-hotrg", action="store_true")
+    ap.add_argument("--svd-bench", type=int, default=0, metavar="S",
+                    help="time the batched SVD routes alone on S random 256 x 256 matrices (16 kept vectors), "
+                         "one warm-up call each, then exit")
     ap.add_argument("--table1", action="store_true",
                     help="per-sample std of Z~ on the paper's 128-spin network (Table 1) instead of the bench line")
     args = ap.parse_args()
@@ -473,6 +497,10 @@ def main():
         dist.init_process_group("nccl")
     if rank == 0 or world == 1:
         build.build()
+    if args.svd_bench:
+        if rank == 0:
+            print(json.dumps(svd_bench(mctrg, torch, args.svd_bench)))
+        return
     if args.table1:
         if rank == 0:
             print(json.dumps({"table1": run_table1(mctrg, np),
