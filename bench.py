@@ -218,10 +218,17 @@ def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_jobs=3, d
             reached += st == 0
             projected += st == mctrg.MCTRG_EUNREACHABLE
         wall = time.perf_counter() - t0
-        lit_lat, lit_sizes = [], []
+        lit_lat, lit_sizes, admissible = [], [], []
         for _ in range(literal_jobs):
             job = _serve_literal(rng)
-            lit_sizes.append("L=%d chi=%d" % (job[2], job[3]))
+            size = "L=%d chi=%d" % (job[2], job[3])
+            # a literal job the footprint admits runs a first round of matrices up to
+            # 1024 on a side (a minute or more); it is reported, not run here
+            fst, _fp = mctrg.mctrg_server_footprint(srv, job[2], job[3], job[5])
+            if fst == 0:
+                admissible.append(size)
+                continue
+            lit_sizes.append(size)
             ts = time.perf_counter()
             st, j = mctrg.mctrg_server_submit(srv, *job)
             if st != 0:
@@ -241,7 +248,7 @@ def measure_serving(mctrg, seconds, load=0.7, seed=0xB0A7 + 5, literal_jobs=3, d
             "latency_p99_s": float(lat[min(len(lat) - 1, int(0.99 * len(lat)))]) if len(lat) else None,
             "trajectories_per_s": n_traj / wall, "jobs_reaching_target": reached,
             "jobs_projected_unreachable": projected, "jobs_unfinished_after_drain": unfinished,
-            "literal_jobs": {"sizes": lit_sizes, "refused_at_submit": refused,
+            "literal_jobs": {"sizes": lit_sizes, "admissible_not_run": admissible, "refused_at_submit": refused,
                              "projected_out_of_reach": int(sum(1 for x in lit if x == mctrg.MCTRG_EUNREACHABLE)),
                              "other_status": [int(x) for x in lit if x != mctrg.MCTRG_EUNREACHABLE],
                              "latency_s": lit_lat},
@@ -577,8 +584,9 @@ def main():
     mixed = None
     if wl["precision"] == 0 and not args.no_mixed:
         mixed = {}
-        ref = np.concatenate([o[0].cpu().numpy() for o in outs])
-        e64 = mctrg.mctrg_merge_estimates(ests)
+        steps_m = min(args.steps, 5)
+        ref = np.concatenate([o[0].cpu().numpy() for o in outs[:steps_m]])
+        e64 = mctrg.mctrg_merge_estimates(ests[:steps_m])
         peaks_m, _ = measured_peaks()
         for name, prec, note, ratio in (
                 ("tf32x3", mctrg.MCTRG_TF32X3, "TF32 hi/lo split, three tcgen05 passes, FP32 accumulation", 0.5),
@@ -587,15 +595,16 @@ def main():
                                                "band reduction (8-bit digits of a fixed-point trailing matrix)",
                  1.0)):
             cm = make_ctx(prec)
-            ms_m, ests_m, outs_m = timed_steps(cm, args.steps, 1, 0)
+            # at most 5 timed steps: these legs compare paths on the same trajectories
+            ms_m, ests_m, outs_m = timed_steps(cm, steps_m, 1, 0)
             gst = mctrg.mctrg_kernel_stats(cm, mctrg.K_GEMM)
             kst = [mctrg.mctrg_kernel_stats(cm, k) for k in range(mctrg.K_COUNT)]
             mctrg.mctrg_destroy(cm)
             got = np.concatenate([o[0].cpu().numpy() for o in outs_m])
             # near-tie trajectories (flagged in either run) may keep different indices: left out,
             # as in the parity tests, and counted
-            fl = np.concatenate([o[2].cpu().numpy() for o in outs]) | np.concatenate([o[2].cpu().numpy()
-                                                                                     for o in outs_m])
+            fl = np.concatenate([o[2].cpu().numpy() for o in outs[:steps_m]]) | np.concatenate(
+                [o[2].cpu().numpy() for o in outs_m])
             ok = np.isfinite(ref) & np.isfinite(got) & (fl == 0)
             rel = np.abs(got[ok] - ref[ok]) / np.abs(ref[ok])
             em = mctrg.mctrg_merge_estimates(ests_m)
@@ -605,8 +614,10 @@ def main():
             tc_rate = passes * gst.flops_alg / (gst.ms / 1e3) / 1e12 if gst.ms > 0 else None
             tc_peak = peaks_m.get("bf16_tflops_sustained", peaks_m.get("bf16_tflops")) * ratio
             mixed[name] = {
-                "precision": note + "; SVD and sampling FP64",
-                "value": B * args.steps * world / (ms_m / 1000.0), "ms_per_step": ms_m / args.steps,
+                "precision": note + ("; SVD and sampling FP64" if prec == mctrg.MCTRG_TF32X3 else
+                                     "; bisection, vectors, chase and sampling FP64"),
+                "steps": steps_m,
+                "value": B * steps_m * world / (ms_m / 1000.0), "ms_per_step": ms_m / steps_m,
                 "lnZ_rel_err_per_traj_median": float(np.median(rel)) if rel.size else None,
                 "lnZ_rel_err_per_traj_max": float(np.max(rel)) if rel.size else None,
                 "lnZ_abs_err_per_site_max": float(np.max(np.abs(got[ok] - ref[ok]))) / wl["L"] ** 2

@@ -462,11 +462,13 @@ const char* mctrg_strerror(int status);
  * not hold; a job passed over 32 times for later, smaller ones blocks the
  * queue until memory frees.  Workers keep their buffers between jobs and
  * give them back only when a queued job is blocked on memory.  A job
- * advances in rounds of trajectories (256 first for L <= 64, 32 for
- * L <= 256, 4 above; doubling up to 8192); after each round it stops when
- * its standard error of ln Z reaches the target, or when that error
- * projected to max_samples by the 1/sqrt(N) law (Sec. V, Eq. shrunkDev)
- * exceeds twice the target (EUNREACHABLE), or when max_samples is spent.
+ * advances in rounds of trajectories (the first about half a second of SVD
+ * work, from the n^3 of the lattice's levels: 2 to 256 trajectories;
+ * doubling up to 8192); after each round it stops when its standard error
+ * of ln Z reaches the target, or when that error projected to max_samples by
+ * the 1/sqrt(N) law (Sec. V, Eq. shrunkDev) exceeds twice the target
+ * (EUNREACHABLE; a merged mean Z~ <= 0 or a non-finite error counts as
+ * unbounded), or when max_samples is spent.
  * The kernels of all running jobs share the device on their streams.
  * Trajectory i of a job uses counter i under the job's seed, so its result
  * is the same alone and in any mix. */

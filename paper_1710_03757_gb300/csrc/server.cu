@@ -122,9 +122,12 @@ struct mctrg_server {
       if (j->target == 0.0) { round = std::min(round * 2, kRoundMax); continue; }   // fixed-sample job
       if (total.status == MCTRG_OK && total.se_ln_Z <= j->target) { reached = true; break; }
       // projection of the standard error to max_samples (1/sqrt(N)); a margin
-      // of 2 absorbs the scatter of an early estimate of it
-      if (total.status == MCTRG_OK && total.n >= std::min<int64_t>(64, j->round0) && std::isfinite(total.se_ln_Z) &&
-          total.se_ln_Z * std::sqrt((double)total.n / (double)j->max_samples) > 2.0 * j->target)
+      // of 2 absorbs the scatter of an early estimate of it.  A round whose
+      // mean Z~ is not positive (EDOMAIN: ln Z^ undefined) or whose SE is not
+      // finite projects as unbounded, so such a job stops after it too
+      const double se = (total.status == MCTRG_OK && std::isfinite(total.se_ln_Z)) ? total.se_ln_Z : INFINITY;
+      if (total.n >= std::min<int64_t>(64, j->round0) &&
+          se * std::sqrt((double)total.n / (double)j->max_samples) > 2.0 * j->target)
         break;
       round = std::min(round * 2, kRoundMax);
     }
