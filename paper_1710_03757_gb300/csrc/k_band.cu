@@ -816,14 +816,23 @@ __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
   const int ntile = (n - k - B + N - 1) / N;
   for (int ct = 0; ct < ntile; ++ct) {
     const int cb = k + B + ct * N;                  // first column of the tile
-    // this warp's 16 columns of the row, loaded before the products run
+    // this warp's 16 columns of the row, loaded before the products run; n and
+    // cw are multiples of 8, so the first 8 exist when cw < n and the second 8
+    // when cw + 8 < n
     const int cw = cb + hc * NH;
     const bool rowok = r < n && el != kZeroExp && cw < n;
+    const bool half2 = cw + 8 < n;
     longlong2* rowp = (longlong2*)(A + (size_t)r * n + cw);
     longlong2 q[NH / 2];
+#pragma unroll
+    for (int i = 0; i < NH / 2; ++i) q[i] = make_longlong2(0, 0);
     if (rowok) {
 #pragma unroll
-      for (int i = 0; i < NH / 2; ++i) q[i] = rowp[i];
+      for (int i = 0; i < NH / 4; ++i) q[i] = rowp[i];
+      if (half2) {
+#pragma unroll
+        for (int i = NH / 4; i < NH / 2; ++i) q[i] = rowp[i];
+      }
     }
     if (t < 2 * N) {                                 // B operand: column c = [Z[:, c] 2^-eA ; U[:, c]]
       const int cc = t & (N - 1), part = t >> 5, c = cb + cc;
@@ -904,7 +913,11 @@ __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
     }
     if (apply) {
 #pragma unroll
-      for (int i = 0; i < NH / 2; ++i) rowp[i] = q[i];
+      for (int i = 0; i < NH / 4; ++i) rowp[i] = q[i];
+      if (half2) {
+#pragma unroll
+        for (int i = NH / 4; i < NH / 2; ++i) rowp[i] = q[i];
+      }
     }
     tc_fence_before();
     __syncthreads();                                 // s_er and the B tiles are rewritten next
