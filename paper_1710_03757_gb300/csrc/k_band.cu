@@ -433,6 +433,7 @@ __global__ void __launch_bounds__(256) k_band_gemm_w(BandArgs a, int k) {
     }
   };
   load(0);
+  int committed = 0;                                 // commits thread 0 issued (the same count in every thread)
   for (int ch = 0; ch < nchunk; ++ch) {
     if (ch > 0 && !mbar_wait(&bar, (ch - 1) & 1)) atomicOr(&s_fail, 1);
     __syncthreads();
@@ -467,6 +468,7 @@ __global__ void __launch_bounds__(256) k_band_gemm_w(BandArgs a, int k) {
       issue_products(tmem, As, kTileBytes, Bs, bt, 1, N, idesc, false);
       umma_commit(&bar);
     }
+    ++committed;
     if (ch + 1 < nchunk) load(ch + 1);
   }
   if (!s_fail && !mbar_wait(&bar, (nchunk - 1) & 1)) atomicOr(&s_fail, 1);
@@ -497,6 +499,9 @@ __global__ void __launch_bounds__(256) k_band_gemm_w(BandArgs a, int k) {
   } else if (s_fail && t == 0) {
     atomicOr(a.err, 1u);
   }
+  // after an expired wait, give the products in flight another bounded wait
+  // before their tensor memory is freed
+  if (s_fail && committed > 0) mbar_wait(&bar, (committed - 1) & 1);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_free(tmem, 128);
@@ -652,6 +657,7 @@ __global__ void __launch_bounds__(256) k_band_gemm_x(BandArgs a, int k) {
     }
   };
   load(0);
+  int committed = 0;                                 // commits thread 0 issued (the same count in every thread)
   for (int ch = 0; ch < nchunk; ++ch) {
     if (ch > 0 && !mbar_wait(&bar, (ch - 1) & 1)) atomicOr(&s_fail, 1);
     __syncthreads();
@@ -686,6 +692,7 @@ __global__ void __launch_bounds__(256) k_band_gemm_x(BandArgs a, int k) {
       issue_products(tmem, As, kTileBytes, Bs, bt, 1, N, idesc, false);
       umma_commit(&bar);
     }
+    ++committed;
     if (ch + 1 < nchunk) load(ch + 1);
   }
   if (!s_fail && !mbar_wait(&bar, (nchunk - 1) & 1)) atomicOr(&s_fail, 1);
@@ -738,6 +745,9 @@ __global__ void __launch_bounds__(256) k_band_gemm_x(BandArgs a, int k) {
   } else if (s_fail && t == 0) {
     atomicOr(a.err, 1u);
   }
+  // after an expired wait, give the products in flight another bounded wait
+  // before their tensor memory is freed
+  if (s_fail && committed > 0) mbar_wait(&bar, (committed - 1) & 1);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_free(tmem, 128);
@@ -814,6 +824,7 @@ __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
   const int quad = warp & 3, hc = warp >> 2;
   const int rho = quad * 32 + lane, r = r0 + rho;
   const int ntile = (n - k - B + N - 1) / N;
+  int committed = 0;                                 // commits thread 0 issued (the same count in every thread)
   for (int ct = 0; ct < ntile; ++ct) {
     const int cb = k + B + ct * N;                  // first column of the tile
     // this warp's 16 columns of the row, loaded before the products run; n and
@@ -862,6 +873,7 @@ __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
       issue_products(tmem, As, kTileBytes, Bs, bt, 0, N, idesc, true);
       umma_commit(&bar);
     }
+    ++committed;
     if (!mbar_wait(&bar, ct & 1)) atomicOr(&s_fail, 1);
     tc_fence_after();
     __syncthreads();
@@ -923,6 +935,9 @@ __global__ void __launch_bounds__(256, 2) k_band_update(BandArgs a, int k) {
     __syncthreads();                                 // s_er and the B tiles are rewritten next
   }
   if (s_fail && t == 0) atomicOr(a.err, 1u);
+  // after an expired wait, give the products in flight another bounded wait
+  // before their tensor memory is freed
+  if (s_fail && committed > 0) mbar_wait(&bar, (committed - 1) & 1);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_free(tmem, 256);
