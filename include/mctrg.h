@@ -416,9 +416,11 @@ int mctrg_svd_bidiag_batched(const double* M, int n, int64_t batch, double* sigm
  * inverse iteration, and the two stages' right reflectors applied back).
  * Arguments, layouts, accuracy and ownership as mctrg_svd_bidiag_batched;
  * n a multiple of 8 with 64 <= n <= 256, 0 <= n_vec <= 16.  The fixed point
- * is set from |M|_F computed in FP64, so a matrix whose squared entries all
- * underflow (every |M_ij| below about 1e-154) is treated as zero; the level
- * matrices of a context are normalized and never come near that.
+ * is set from |M|_F computed in FP64, so the entries must keep their squares
+ * in range: a matrix whose squared entries all underflow (every |M_ij| below
+ * about 1e-154) is treated as zero, and one with entries above about 1e154
+ * is not supported; the level matrices of a context are normalized and never
+ * come near either.
  * Errors: EINVAL, ENOMEM, ECUDA (also when a tensor-core kernel's bounded
  * wait expired). */
 int mctrg_svd_band_batched(const double* M, int n, int64_t batch, double* sigma, int n_vec,
